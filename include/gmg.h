@@ -1,0 +1,199 @@
+/*
+ * gmg.h -- C ABI of the GB300 geometric-multigrid solve library (libgmg.so).
+ *
+ * Method: the multigrid solver of Wiersma, Nasikun, Eisemann, Hildebrandt,
+ * "A Fast Geometric Multigrid Method for Curved Surfaces" (SIGGRAPH 2023):
+ *   Alg. 1  setup A_{l+1} = P_l^T A_l P_l, then repeat V-cycles until
+ *           ||A x - b|| <= eps ||b||;
+ *   Alg. 2  V-cycle: Gauss-Seidel pre-relaxation, residual, restriction by
+ *           P_l^T, recursive coarse correction with zero initial guess,
+ *           prolongation by P_l, post-relaxation; direct solve on the
+ *           coarsest level;
+ *   Sec. 4  prolongations with at most three entries per row (an INPUT here).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a gmg_status; GMG_OK on success.  On failure
+ *     gmg_last_error() returns a human-readable message for the calling
+ *     thread.  No entry point traps, aborts or waits without bound.
+ *   - "host" arrays are ordinary CPU memory, read (or written) only during the
+ *     call.  "device" arrays are CUDA global-memory pointers on the handle's
+ *     device; results in device arrays are ready once work queued on `stream`
+ *     before the call returns has completed.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - The library copies and owns everything setup needs; caller buffers are
+ *     borrowed only for the duration of a call.  One handle must not be used
+ *     from two host threads, or on two streams, at the same time.
+ *   - Vectors exchanged through the API are in the caller's row numbering
+ *     (the numbering of the A and P_l given to gmg_setup); internal colour
+ *     permutations are never visible.
+ *   - Indices are 0-based.
+ */
+#ifndef GMG_H
+#define GMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gmg_ctx *gmg_handle;
+
+typedef enum {
+  GMG_OK = 0,
+  GMG_ERR_INVALID_ARG = 1,    /* bad pointer, size, index or option          */
+  GMG_ERR_NOT_SPD = 2,        /* A: a diagonal entry <= 0 or A != A^T        */
+  GMG_ERR_EMPTY_P_COLUMN = 3, /* a coarse point no fine row maps to: its
+                                 Galerkin diagonal would be 0 (the NaN rows
+                                 the paper reports for its experiments)      */
+  GMG_ERR_CHOLESKY = 4,       /* coarsest operator not positive definite     */
+  GMG_ERR_NOT_CONVERGED = 5,  /* max_iter reached; x holds the last iterate  */
+  GMG_ERR_NONFINITE = 6,      /* NaN/Inf in an input or in an iterate        */
+  GMG_ERR_OOM = 7,            /* device allocation failed                    */
+  GMG_ERR_CUDA = 8,           /* a CUDA runtime call failed                  */
+  GMG_ERR_TIMEOUT = 9,        /* a bounded device-side wait gave up          */
+  GMG_ERR_TOO_LARGE = 10      /* a size exceeds a documented limit           */
+} gmg_status;
+
+/* Arithmetic of the V-cycle inside gmg_solve. */
+enum {
+  GMG_FP64 = 0,        /* plain Alg. 1: FP64 V-cycles, x <- MGI(x, b, 1)       */
+  GMG_FP32_REFINE = 1, /* FP64 iterative refinement: r = b - A x (FP64),
+                          e = MGI(0, r, 1) in FP32 (coarsest solve FP64),
+                          x += e; identical to GMG_FP64 in exact arithmetic   */
+  GMG_FP32_PCG = 2     /* FP64 conjugate gradients preconditioned by one FP32
+                          V-cycle per iteration (flexible Polak-Ribiere beta)  */
+};
+
+enum { GMG_MEM_DEVICE = 0, GMG_MEM_HOST = 1 };
+
+/* System matrix A (host).  n x n, CSR with 64-bit row pointers, sorted and
+ * unique column indices per row, the diagonal present in every row.  A must be
+ * symmetric with a positive diagonal (A = M + tL of the paper's Eq.
+ * (smoothing) or Eq. (Poisson)). */
+typedef struct {
+  int64_t n;
+  const int64_t *rowptr; /* n + 1 */
+  const int32_t *col;    /* rowptr[n] */
+  const double *val;     /* rowptr[n] */
+} gmg_csr;
+
+/* Prolongation P_l in R^{n_fine x n_coarse} (host), Sec. 4.4: row i holds
+ * three (index, weight) slots idx[3i+s], w[3i+s], s = 0..2.  A slot with
+ * w == 0 is unused (its index must still be in [0, n_coarse)).  The non-zero
+ * slots of a row must name distinct coarse points.  Every coarse point must
+ * appear in some row with w != 0. */
+typedef struct {
+  int64_t n_fine, n_coarse;
+  const int32_t *idx; /* 3 * n_fine */
+  const double *w;    /* 3 * n_fine */
+} gmg_prolong;
+
+typedef struct {
+  int precision;  /* GMG_FP64 | GMG_FP32_REFINE | GMG_FP32_PCG (default REFINE) */
+  int nu_pre;     /* Gauss-Seidel sweeps before the coarse correction (2)     */
+  int nu_post;    /* sweeps after it (2)                                      */
+  int max_iter;   /* outer iterations (100)                                   */
+  int post_forward; /* 0: post-relaxation visits colours in descending order
+                       (symmetric cycle, required by GMG_FP32_PCG); 1: ascending */
+  int use_graphs; /* 1: replay each cycle from a captured CUDA graph (default)  */
+} gmg_options;
+
+typedef struct {
+  int iters;          /* V-cycles (or PCG iterations) performed              */
+  double rel_res;     /* final ||b - A x||_2 / ||b||_2, in FP64              */
+  double *history;    /* optional host buffer: history[k] = relative residual
+                         after k iterations, history[0] for the initial guess */
+  int history_cap;    /* capacity of `history` in doubles                    */
+} gmg_solve_info;
+
+/* Fills `opt` with the defaults listed above. */
+void gmg_default_options(gmg_options *opt);
+
+/* Static text for a status code. */
+const char *gmg_status_string(gmg_status s);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *gmg_last_error(void);
+
+/* Alg. 1 setup.  Copies A and the `n_prolong` prolongations (finest first;
+ * P[l].n_fine must equal the size of level l), computes every Galerkin level
+ * A_{l+1} = P_l^T A_l P_l on the GPU (two-pass symbolic + numeric product,
+ * mirrored to exact symmetry), colours every level (greedy first fit in
+ * increasing row index), lays the levels out colour by colour, and factors the
+ * coarsest level with a dense FP64 Cholesky.  `opt` may be NULL (defaults).
+ * On success *h owns all device memory of the hierarchy; release it with
+ * gmg_destroy.  Errors: INVALID_ARG, NOT_SPD, EMPTY_P_COLUMN, CHOLESKY,
+ * NONFINITE, TOO_LARGE (coarsest level above 8192 rows, or a Galerkin row with
+ * more than 768 entries), OOM, CUDA. */
+gmg_status gmg_setup(gmg_handle *h, const gmg_csr *A, int n_prolong, const gmg_prolong *P,
+                     const gmg_options *opt, void *stream);
+
+/* Numeric refresh: new values for A on the SAME sparsity pattern (`val` has
+ * rowptr[n] entries in the pattern's order; host or device per `mem`).
+ * Recomputes every Galerkin level and the coarsest factor on the GPU without
+ * touching the host-side structure.  Errors: NOT_SPD, CHOLESKY, NONFINITE. */
+gmg_status gmg_set_values(gmg_handle h, const double *val, int mem, void *stream);
+
+/* Alg. 1 iteration: solves A x = b to ||b - A x||_2 <= tol ||b||_2.  `x` holds
+ * the initial guess on entry and the solution on exit (n doubles, host or
+ * device per `mem`).  b == 0 gives x = 0 after 0 iterations.  `info` may be
+ * NULL.  Errors: NOT_CONVERGED (x = last iterate), NONFINITE, INVALID_ARG. */
+gmg_status gmg_solve(gmg_handle h, const double *b, double *x, double tol, int mem, gmg_solve_info *info,
+                     void *stream);
+
+/* Batched right-hand sides: B and X are n x nrhs, row-major (element (i, c)
+ * at i * nrhs + c), host or device per `mem`.  Every column is solved to the
+ * same tolerance with FP32 V-cycles that read each matrix once for all
+ * columns, inside FP64 refinement.  1 <= nrhs <= 16. */
+gmg_status gmg_solve_batched(gmg_handle h, int nrhs, const double *B, double *X, double tol, int mem,
+                             gmg_solve_info *info, void *stream);
+
+/* Releases the handle and its device memory.  NULL is accepted. */
+gmg_status gmg_destroy(gmg_handle h);
+
+/* ---- kernel timing (measurement support, not part of the method) ----
+ * With profiling enabled, gmg_solve records CUDA events on its stream around
+ * the finest level's pre- and post-smoothing blocks and around every finest
+ * V-cycle (inside captured graphs as external event nodes).
+ * gmg_profile_read returns the sums since the last read and resets them:
+ * out[0] = ms spent in finest-level smoothing blocks, out[1] = Gauss-Seidel
+ * colour launches in them, out[2] = ms spent in V-cycles, out[3] = V-cycles. */
+gmg_status gmg_profile(gmg_handle h, int enable);
+/* Number of this library's CUDA kernels launched from the calling thread so
+ * far (each replay of a captured graph counts its kernel nodes). */
+uint64_t gmg_kernel_launches(void);
+gmg_status gmg_profile_read(gmg_handle h, double *out /* 4 */);
+
+/* ---- introspection (host outputs) ---- */
+gmg_status gmg_num_levels(gmg_handle h, int *nlev);
+/* rows, stored entries (diagonal included) and colours of level l. */
+gmg_status gmg_level_info(gmg_handle h, int l, int64_t *n, int64_t *nnz, int *ncolors);
+/* Copies level l's Galerkin operator A_l (CSR, caller numbering, rowptr n+1,
+ * col/val nnz) and its colouring (n) into host buffers; any may be NULL. */
+gmg_status gmg_level_export(gmg_handle h, int l, int64_t *rowptr, int32_t *col, double *val, int32_t *color);
+
+/* ---- single steps of Alg. 2 on device vectors in the caller's numbering of
+ * level l (FP64 arrays; with fp32 != 0 the step runs on the FP32 copy of the
+ * level: inputs are rounded to FP32 and outputs widened back).  These are the
+ * kernels the solve runs, exposed for step-by-step checks. ---- */
+
+/* `nsweep` multicolour Gauss-Seidel sweeps on A_l x = b, colours ascending
+ * (descending != 0: descending).  x is updated in place. */
+gmg_status gmg_smooth(gmg_handle h, int l, int fp32, const double *b, double *x, int nsweep, int descending,
+                      void *stream);
+/* r = b - A_l x. */
+gmg_status gmg_residual(gmg_handle h, int l, int fp32, const double *x, const double *b, double *r, void *stream);
+/* bc = P_l^T r  (bc has n_{l+1} entries). */
+gmg_status gmg_restrict(gmg_handle h, int l, int fp32, const double *r, double *bc, void *stream);
+/* x += P_l u  (u has n_{l+1} entries). */
+gmg_status gmg_prolong_add(gmg_handle h, int l, int fp32, const double *u, double *x, void *stream);
+/* x = A_lambda^-1 b on the coarsest level (FP64 factor in both modes). */
+gmg_status gmg_coarse_solve(gmg_handle h, int fp32, const double *b, double *x, void *stream);
+/* One V-cycle x <- MGI(x, b, 1) of Alg. 2 on the finest level. */
+gmg_status gmg_vcycle(gmg_handle h, int fp32, const double *b, double *x, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GMG_H */

@@ -1,0 +1,288 @@
+"""Python binding of libgmg: the GPU multigrid solve of Wiersma et al.,
+"A Fast Geometric Multigrid Method for Curved Surfaces" (SIGGRAPH 2023).
+
+This module only marshals arguments to the C ABI declared in include/gmg.h
+(ctypes; no torch types cross the boundary).  Every step of the solve runs in
+the library's CUDA kernels; there is no CPU fallback: importing works without
+the library, but constructing a Solver raises when libgmg.so is missing.
+
+Device vectors are torch CUDA tensors (float64, contiguous); host vectors are
+numpy arrays.  The stream is torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB, build_library  # noqa: F401
+
+GMG_OK, GMG_ERR_INVALID_ARG, GMG_ERR_NOT_SPD, GMG_ERR_EMPTY_P_COLUMN, GMG_ERR_CHOLESKY, GMG_ERR_NOT_CONVERGED, \
+    GMG_ERR_NONFINITE, GMG_ERR_OOM, GMG_ERR_CUDA, GMG_ERR_TIMEOUT, GMG_ERR_TOO_LARGE = range(11)
+GMG_FP64, GMG_FP32_REFINE, GMG_FP32_PCG = 0, 1, 2
+GMG_MEM_DEVICE, GMG_MEM_HOST = 0, 1
+
+EXPORTED = [
+    "gmg_default_options", "gmg_status_string", "gmg_last_error", "gmg_setup", "gmg_set_values", "gmg_solve",
+    "gmg_solve_batched", "gmg_destroy", "gmg_num_levels", "gmg_level_info", "gmg_level_export", "gmg_smooth",
+    "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_coarse_solve", "gmg_vcycle", "gmg_profile",
+    "gmg_profile_read", "gmg_kernel_launches",
+]
+
+
+def kernel_launches() -> int:
+    """Kernels libgmg has launched from this thread so far."""
+    return int(load_library().gmg_kernel_launches())
+
+
+class gmg_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("val", ctypes.c_void_p)]
+
+
+class gmg_prolong(ctypes.Structure):
+    _fields_ = [("n_fine", ctypes.c_int64), ("n_coarse", ctypes.c_int64), ("idx", ctypes.c_void_p),
+                ("w", ctypes.c_void_p)]
+
+
+class gmg_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("post_forward", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+
+
+class gmg_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double), ("history", ctypes.c_void_p),
+                ("history_cap", ctypes.c_int)]
+
+
+class GMGError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Loads libgmg.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise OSError(f"libgmg.so not found at {path}; build it with paper_2307_04886_gb300.build_library()")
+    lib = ctypes.CDLL(path)
+    V, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    sig = {
+        "gmg_default_options": (None, [V]),
+        "gmg_status_string": (ctypes.c_char_p, [I]),
+        "gmg_last_error": (ctypes.c_char_p, []),
+        "gmg_setup": (I, [V, V, I, V, V, V]),
+        "gmg_set_values": (I, [V, V, I, V]),
+        "gmg_solve": (I, [V, V, V, D, I, V, V]),
+        "gmg_solve_batched": (I, [V, I, V, V, D, I, V, V]),
+        "gmg_destroy": (I, [V]),
+        "gmg_num_levels": (I, [V, V]),
+        "gmg_level_info": (I, [V, I, V, V, V]),
+        "gmg_level_export": (I, [V, I, V, V, V, V]),
+        "gmg_smooth": (I, [V, I, I, V, V, I, I, V]),
+        "gmg_residual": (I, [V, I, I, V, V, V, V]),
+        "gmg_restrict": (I, [V, I, I, V, V, V]),
+        "gmg_prolong_add": (I, [V, I, I, V, V, V]),
+        "gmg_coarse_solve": (I, [V, I, V, V, V]),
+        "gmg_vcycle": (I, [V, I, V, V, V]),
+        "gmg_profile": (I, [V, I]),
+        "gmg_kernel_launches": (ctypes.c_uint64, []),
+        "gmg_profile_read": (I, [V, V]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str, ok=(GMG_OK,)):
+    if st not in ok:
+        raise GMGError(st, where, load_library().gmg_last_error().decode())
+    return st
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t, n: int | None = None):
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """A multigrid hierarchy on the GPU (gmg_setup).
+
+    A: scipy sparse matrix (symmetric, sorted CSR with the diagonal present).
+    Ps: prolongations, finest first, each with n_coarse, idx [n,3] int32 and
+        w [n,3] float64 (three slots per row, weight 0 = unused slot).
+    """
+
+    def __init__(self, A, Ps, precision: int = GMG_FP32_REFINE, nu_pre: int = 2, nu_post: int = 2,
+                 max_iter: int = 100, post_forward: bool = False, use_graphs: bool = True):
+        import scipy.sparse as sp
+
+        lib = load_library()
+        A = sp.csr_matrix(A)
+        A.sort_indices()
+        self.n = A.shape[0]
+        self._rp = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        self._ci = np.ascontiguousarray(A.indices, dtype=np.int32)
+        self._va = np.ascontiguousarray(A.data, dtype=np.float64)
+        csr = gmg_csr(self.n, _np_ptr(self._rp).value, _np_ptr(self._ci).value, _np_ptr(self._va).value)
+        keep, arr = [], (gmg_prolong * max(1, len(Ps)))()
+        nf = self.n
+        for l, P in enumerate(Ps):
+            idx = np.ascontiguousarray(P.idx, dtype=np.int32)
+            w = np.ascontiguousarray(P.w, dtype=np.float64)
+            keep += [idx, w]
+            arr[l] = gmg_prolong(nf, P.n_coarse, _np_ptr(idx).value, _np_ptr(w).value)
+            nf = P.n_coarse
+        opt = gmg_options(precision, nu_pre, nu_post, max_iter, int(post_forward), int(use_graphs))
+        self._opt = opt
+        h = ctypes.c_void_p()
+        _check(lib.gmg_setup(ctypes.byref(h), ctypes.byref(csr), len(Ps), arr, ctypes.byref(opt), _stream()),
+               "gmg_setup")
+        self._h = h
+        self._lib = lib
+        nl = ctypes.c_int()
+        lib.gmg_num_levels(h, ctypes.byref(nl))
+        self.nlev = nl.value
+        self.dims = []
+        for l in range(self.nlev):
+            n, nnz, nc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+            lib.gmg_level_info(h, l, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(nc))
+            self.dims.append((n.value, nnz.value, nc.value))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.gmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ---- whole solves ----
+    def solve(self, b, x=None, tol: float = 1e-10, history: int = 0, raise_on_fail: bool = True):
+        """Solves A x = b.  b/x: CUDA float64 tensors (device path) or numpy
+        arrays (host path).  Returns (x, iters, rel_res, history, status)."""
+        import torch
+
+        hist = np.zeros(max(1, history))
+        info = gmg_solve_info(0, 0.0, _np_ptr(hist).value if history else None, history)
+        if isinstance(b, torch.Tensor):
+            xx = torch.zeros_like(b) if x is None else x
+            st = self._lib.gmg_solve(self._h, _dptr(b, self.n), _dptr(xx, self.n), tol, GMG_MEM_DEVICE,
+                                     ctypes.byref(info), _stream())
+        else:
+            bb = np.ascontiguousarray(b, dtype=np.float64)
+            xx = np.zeros(self.n) if x is None else np.ascontiguousarray(x, dtype=np.float64).copy()
+            st = self._lib.gmg_solve(self._h, _np_ptr(bb), _np_ptr(xx), tol, GMG_MEM_HOST, ctypes.byref(info),
+                                     _stream())
+        if raise_on_fail:
+            _check(st, "gmg_solve")
+        return xx, info.iters, info.rel_res, hist[: min(history, info.iters + 1)], st
+
+    def solve_batched(self, B, X=None, tol: float = 1e-10, history: int = 0, raise_on_fail: bool = True):
+        import torch
+
+        hist = np.zeros(max(1, history))
+        info = gmg_solve_info(0, 0.0, _np_ptr(hist).value if history else None, history)
+        if isinstance(B, torch.Tensor):
+            nrhs = B.shape[1]
+            XX = torch.zeros_like(B) if X is None else X
+            st = self._lib.gmg_solve_batched(self._h, nrhs, _dptr(B), _dptr(XX), tol, GMG_MEM_DEVICE,
+                                             ctypes.byref(info), _stream())
+        else:
+            BB = np.ascontiguousarray(B, dtype=np.float64)
+            nrhs = BB.shape[1]
+            XX = np.zeros_like(BB) if X is None else np.ascontiguousarray(X, dtype=np.float64).copy()
+            st = self._lib.gmg_solve_batched(self._h, nrhs, _np_ptr(BB), _np_ptr(XX), tol, GMG_MEM_HOST,
+                                             ctypes.byref(info), _stream())
+        if raise_on_fail:
+            _check(st, "gmg_solve_batched")
+        return XX, info.iters, info.rel_res, hist[: min(history, info.iters + 1)], st
+
+    def set_values(self, val):
+        import torch
+
+        if isinstance(val, torch.Tensor):
+            _check(self._lib.gmg_set_values(self._h, _dptr(val), GMG_MEM_DEVICE, _stream()), "gmg_set_values")
+        else:
+            v = np.ascontiguousarray(val, dtype=np.float64)
+            _check(self._lib.gmg_set_values(self._h, _np_ptr(v), GMG_MEM_HOST, _stream()), "gmg_set_values")
+
+    def profile(self, enable: bool = True):
+        _check(self._lib.gmg_profile(self._h, int(enable)), "gmg_profile")
+
+    def profile_read(self):
+        """(finest smoothing ms, GS launches, V-cycle ms, V-cycles) since the last read."""
+        out = np.zeros(4)
+        _check(self._lib.gmg_profile_read(self._h, _np_ptr(out)), "gmg_profile_read")
+        return tuple(float(v) for v in out)
+
+    # ---- introspection ----
+    def level(self, l: int):
+        """(A_l as scipy CSR in caller numbering, colour of every row)."""
+        import scipy.sparse as sp
+
+        n, nnz, _ = self.dims[l]
+        rp, ci, va, col = np.empty(n + 1, np.int64), np.empty(nnz, np.int32), np.empty(nnz), np.empty(n, np.int32)
+        _check(self._lib.gmg_level_export(self._h, l, _np_ptr(rp), _np_ptr(ci), _np_ptr(va), _np_ptr(col)),
+               "gmg_level_export")
+        return sp.csr_matrix((va, ci, rp), shape=(n, n)), col
+
+    # ---- single steps of Alg. 2 (device tensors, caller numbering) ----
+    def smooth(self, l, x, b, nsweep, descending=False, fp32=False):
+        _check(self._lib.gmg_smooth(self._h, l, int(fp32), _dptr(b), _dptr(x), nsweep, int(descending), _stream()),
+               "gmg_smooth")
+        return x
+
+    def residual(self, l, x, b, r, fp32=False):
+        _check(self._lib.gmg_residual(self._h, l, int(fp32), _dptr(x), _dptr(b), _dptr(r), _stream()),
+               "gmg_residual")
+        return r
+
+    def restrict(self, l, r, bc, fp32=False):
+        _check(self._lib.gmg_restrict(self._h, l, int(fp32), _dptr(r), _dptr(bc), _stream()), "gmg_restrict")
+        return bc
+
+    def prolong_add(self, l, u, x, fp32=False):
+        _check(self._lib.gmg_prolong_add(self._h, l, int(fp32), _dptr(u), _dptr(x), _stream()), "gmg_prolong_add")
+        return x
+
+    def coarse_solve(self, b, x, fp32=False):
+        _check(self._lib.gmg_coarse_solve(self._h, int(fp32), _dptr(b), _dptr(x), _stream()), "gmg_coarse_solve")
+        return x
+
+    def vcycle(self, x, b, fp32=False):
+        _check(self._lib.gmg_vcycle(self._h, int(fp32), _dptr(b), _dptr(x), _stream()), "gmg_vcycle")
+        return x

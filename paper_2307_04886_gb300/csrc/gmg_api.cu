@@ -1,0 +1,413 @@
+// extern "C" entry points of libgmg (declared in include/gmg.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+
+#include "gmg_cycle.cuh"
+
+namespace gmg {
+extern thread_local std::string g_last_error;
+
+static gmg_status check_handle(gmg_handle h) {
+  if (!h) {
+    set_error("null handle");
+    return GMG_ERR_INVALID_ARG;
+  }
+  GMG_CK(cudaSetDevice(h->device));
+  return GMG_OK;
+}
+
+// Runs one iteration body, from a captured graph when enabled.
+static gmg_status run_body(gmg_ctx* c, int mode, int seg, cudaStream_t s) {
+  if (!c->opt.use_graphs) return iteration_body(c, mode, seg, s);
+  const int key = mode * 2 + seg;
+  if (!c->graphs[key]) {
+    if (!c->g_stream) GMG_CK(cudaStreamCreateWithFlags(&c->g_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    const uint64_t before = g_launches;
+    GMG_CK(cudaStreamBeginCapture(c->g_stream, cudaStreamCaptureModeThreadLocal));
+    gmg_status st = iteration_body(c, mode, seg, c->g_stream);
+    cudaError_t e = cudaStreamEndCapture(c->g_stream, &g);
+    c->graph_kernels[key] = g_launches - before;  // captured, not yet run
+    g_launches = before;
+    if (st != GMG_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    GMG_CK(e);
+    cudaError_t ei = cudaGraphInstantiate(&c->graphs[key], g, 0);
+    cudaGraphDestroy(g);
+    GMG_CK(ei);
+  }
+  GMG_CK(cudaGraphLaunch(c->graphs[key], s));
+  g_launches += c->graph_kernels[key];
+  return GMG_OK;
+}
+
+static gmg_status fetch_scalars(gmg_ctx* c, cudaStream_t s) {
+  GMG_CK(cudaMemcpyAsync(c->h_scal, c->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GMG_CK(cudaStreamSynchronize(s));
+  if (c->prof && c->prof_pending) {  // the last cycle's events have completed
+    float a = 0, b = 0, v = 0;
+    GMG_CK(cudaEventElapsedTime(&a, c->ev[0], c->ev[1]));
+    GMG_CK(cudaEventElapsedTime(&b, c->ev[2], c->ev[3]));
+    GMG_CK(cudaEventElapsedTime(&v, c->ev[4], c->ev[5]));
+    const Level& L = c->L[0];
+    c->prof_acc[0] += a + b;
+    c->prof_acc[1] += (double)L.ncolor * (c->opt.nu_pre + c->opt.nu_post);
+    c->prof_acc[2] += v;
+    c->prof_acc[3] += 1;
+    c->prof_pending = false;
+  }
+  return GMG_OK;
+}
+
+static gmg_status run_cycle_body(gmg_ctx* c, int mode, int seg, cudaStream_t s) {
+  GMG_TRY(run_body(c, mode, seg, s));
+  if (c->nlev > 1 && (mode != GMG_FP32_PCG || seg == 1)) c->prof_pending = c->prof;
+  return GMG_OK;
+}
+
+// Copies an n-vector in caller numbering (host or device) into the permuted
+// device vector `dst` of level l.
+static gmg_status load_vec(gmg_ctx* c, int l, const double* src, int mem, double* dst, double* stage,
+                           cudaStream_t s) {
+  Level& L = c->L[l];
+  if (mem == GMG_MEM_HOST) {
+    GMG_CK(cudaMemcpyAsync(stage, src, sizeof(double) * (size_t)L.n, cudaMemcpyHostToDevice, s));
+    src = stage;
+  }
+  return launch_gather(L.n, L.perm, src, dst, s);
+}
+
+static gmg_status store_vec(gmg_ctx* c, int l, const double* src, double* dst, int mem, double* stage,
+                            cudaStream_t s) {
+  Level& L = c->L[l];
+  if (mem == GMG_MEM_HOST) {
+    GMG_TRY(launch_scatter(L.n, L.perm, src, stage, s));
+    GMG_CK(cudaMemcpyAsync(dst, stage, sizeof(double) * (size_t)L.n, cudaMemcpyDeviceToHost, s));
+    GMG_CK(cudaStreamSynchronize(s));
+    return GMG_OK;
+  }
+  return launch_scatter(L.n, L.perm, src, dst, s);
+}
+
+}  // namespace gmg
+
+using namespace gmg;
+
+extern "C" {
+
+void gmg_default_options(gmg_options* opt) {
+  if (!opt) return;
+  opt->precision = GMG_FP32_REFINE;
+  opt->nu_pre = 2;
+  opt->nu_post = 2;
+  opt->max_iter = 100;
+  opt->post_forward = 0;
+  opt->use_graphs = 1;
+}
+
+const char* gmg_status_string(gmg_status s) {
+  switch (s) {
+    case GMG_OK: return "ok";
+    case GMG_ERR_INVALID_ARG: return "invalid argument";
+    case GMG_ERR_NOT_SPD: return "matrix not symmetric positive definite";
+    case GMG_ERR_EMPTY_P_COLUMN: return "empty prolongation column";
+    case GMG_ERR_CHOLESKY: return "coarsest Cholesky factorisation failed";
+    case GMG_ERR_NOT_CONVERGED: return "not converged";
+    case GMG_ERR_NONFINITE: return "non-finite value";
+    case GMG_ERR_OOM: return "out of device memory";
+    case GMG_ERR_CUDA: return "CUDA error";
+    case GMG_ERR_TIMEOUT: return "device wait timed out";
+    case GMG_ERR_TOO_LARGE: return "size limit exceeded";
+  }
+  return "unknown status";
+}
+
+const char* gmg_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t gmg_kernel_launches(void) { return g_launches; }
+
+gmg_status gmg_destroy(gmg_handle h) {
+  if (!h) return GMG_OK;
+  cudaSetDevice(h->device);
+  for (auto& g : h->graphs)
+    if (g) cudaGraphExecDestroy(g);
+  if (h->g_stream) cudaStreamDestroy(h->g_stream);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  if (h->h_scal) cudaFreeHost(h->h_scal);
+  cudaDeviceSynchronize();
+  h->arena.release();
+  delete h;
+  return GMG_OK;
+}
+
+gmg_status gmg_setup(gmg_handle* h, const gmg_csr* A, int n_prolong, const gmg_prolong* P, const gmg_options* opt,
+                     void* stream) {
+  g_last_error.clear();
+  if (!h || n_prolong < 0 || (n_prolong > 0 && !P)) {
+    set_error("gmg_setup: null output handle or bad prolongation list");
+    return GMG_ERR_INVALID_ARG;
+  }
+  *h = nullptr;
+  gmg_ctx* c = new (std::nothrow) gmg_ctx();
+  if (!c) return GMG_ERR_OOM;
+  if (opt) c->opt = *opt;
+  else gmg_default_options(&c->opt);
+  if (c->opt.nu_pre < 0 || c->opt.nu_post < 0 || c->opt.max_iter < 0 || c->opt.precision < GMG_FP64 ||
+      c->opt.precision > GMG_FP32_PCG) {
+    set_error("gmg_setup: invalid options");
+    delete c;
+    return GMG_ERR_INVALID_ARG;
+  }
+  gmg_status st = setup_impl(c, A, n_prolong, P, (cudaStream_t)stream);
+  if (st != GMG_OK) {
+    std::string keep = g_last_error;
+    gmg_destroy(c);
+    g_last_error = keep;
+    return st;
+  }
+  *h = c;
+  return GMG_OK;
+}
+
+gmg_status gmg_set_values(gmg_handle h, const double* val, int mem, void* stream) {
+  GMG_TRY(check_handle(h));
+  if (!val) {
+    set_error("gmg_set_values: null values");
+    return GMG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Level& L0 = h->L[0];
+  GMG_CK(cudaMemcpyAsync(L0.csr_val, val, sizeof(double) * (size_t)L0.nnz,
+                         mem == GMG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  return numeric_setup(h, s);
+}
+
+gmg_status gmg_solve(gmg_handle h, const double* b, double* x, double tol, int mem, gmg_solve_info* info,
+                     void* stream) {
+  GMG_TRY(check_handle(h));
+  if (!b || !x || !(tol >= 0.0) || (mem != GMG_MEM_HOST && mem != GMG_MEM_DEVICE)) {
+    set_error("gmg_solve: null vector, negative tolerance or bad memory kind");
+    return GMG_ERR_INVALID_ARG;
+  }
+  gmg_ctx* c = h;
+  cudaStream_t s = (cudaStream_t)stream;
+  Level& L0 = c->L[0];
+  const int64_t n = L0.n;
+  GMG_TRY(load_vec(c, 0, b, mem, c->bs, c->io, s));
+  GMG_TRY(load_vec(c, 0, x, mem, c->xs, c->io2, s));
+  GMG_TRY(norm_b(c, s));
+  GMG_TRY(outer_residual_norm(c, s));
+  GMG_TRY(fetch_scalars(c, s));
+  const double nb = std::sqrt(c->h_scal[S_NB2]);
+  int k = 0;
+  double rel = 0.0;
+  gmg_status st = GMG_ERR_NOT_CONVERGED;
+  auto record = [&](int kk, double v) {
+    if (info && info->history && kk < info->history_cap) info->history[kk] = v;
+  };
+  if (!std::isfinite(nb)) {
+    set_error("gmg_solve: non-finite right-hand side");
+    st = GMG_ERR_NONFINITE;
+  } else if (nb == 0.0) {
+    GMG_CK(cudaMemsetAsync(c->xs, 0, sizeof(double) * (size_t)n, s));
+    record(0, 0.0);
+    st = GMG_OK;
+  } else {
+    rel = std::sqrt(c->h_scal[S_RR]) / nb;
+    record(0, rel);
+    const int mode = c->nlev == 1 ? GMG_FP64 : c->opt.precision;
+    if (!std::isfinite(rel)) {
+      set_error("gmg_solve: non-finite initial residual");
+      st = GMG_ERR_NONFINITE;
+    } else {
+      if (mode == GMG_FP32_PCG) GMG_TRY(pcg_start(c, s));
+      while (k < c->opt.max_iter) {
+        GMG_TRY(run_cycle_body(c, mode, 0, s));
+        GMG_TRY(fetch_scalars(c, s));
+        ++k;
+        rel = std::sqrt(c->h_scal[S_RR]) / nb;
+        if (!std::isfinite(rel)) {
+          set_error("gmg_solve: iterate became non-finite");
+          st = GMG_ERR_NONFINITE;
+          break;
+        }
+        if (rel <= tol && mode == GMG_FP32_PCG) {  // confirm on the true residual
+          GMG_TRY(outer_residual_norm(c, s));
+          GMG_TRY(fetch_scalars(c, s));
+          rel = std::sqrt(c->h_scal[S_RR]) / nb;
+          record(k, rel);
+          if (rel <= tol) {
+            st = GMG_OK;
+            break;
+          }
+          GMG_TRY(pcg_start(c, s));  // restart from the current iterate
+          continue;
+        }
+        record(k, rel);
+        if (rel <= tol) {
+          st = GMG_OK;
+          break;
+        }
+        if (mode == GMG_FP32_PCG) GMG_TRY(run_cycle_body(c, mode, 1, s));
+      }
+      if (st == GMG_ERR_NOT_CONVERGED) set_error("gmg_solve: max_iter reached");
+    }
+  }
+  GMG_TRY(store_vec(c, 0, c->xs, x, mem, c->io2, s));
+  if (info) {
+    info->iters = k;
+    info->rel_res = rel;
+  }
+  return st;
+}
+
+gmg_status gmg_profile(gmg_handle h, int enable) {
+  GMG_TRY(check_handle(h));
+  if ((enable != 0) == h->prof) return GMG_OK;
+  if (enable && !h->ev[0])
+    for (auto& e : h->ev) GMG_CK(cudaEventCreate(&e));
+  for (auto& g : h->graphs)  // re-capture with or without the event nodes
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  h->prof = enable != 0;
+  h->prof_pending = false;
+  return GMG_OK;
+}
+
+gmg_status gmg_profile_read(gmg_handle h, double* out) {
+  if (!h || !out) return GMG_ERR_INVALID_ARG;
+  for (int k = 0; k < 4; ++k) {
+    out[k] = h->prof_acc[k];
+    h->prof_acc[k] = 0.0;
+  }
+  return GMG_OK;
+}
+
+gmg_status gmg_num_levels(gmg_handle h, int* nlev) {
+  if (!h || !nlev) return GMG_ERR_INVALID_ARG;
+  *nlev = h->nlev;
+  return GMG_OK;
+}
+
+gmg_status gmg_level_info(gmg_handle h, int l, int64_t* n, int64_t* nnz, int* ncolors) {
+  if (!h || l < 0 || l >= h->nlev) return GMG_ERR_INVALID_ARG;
+  if (n) *n = h->L[l].n;
+  if (nnz) *nnz = h->L[l].nnz;
+  if (ncolors) *ncolors = h->L[l].ncolor;
+  return GMG_OK;
+}
+
+gmg_status gmg_level_export(gmg_handle h, int l, int64_t* rowptr, int32_t* col, double* val, int32_t* color) {
+  GMG_TRY(check_handle(h));
+  if (l < 0 || l >= h->nlev) return GMG_ERR_INVALID_ARG;
+  Level& L = h->L[l];
+  GMG_CK(cudaDeviceSynchronize());
+  if (rowptr) GMG_CK(cudaMemcpy(rowptr, L.csr_rowptr, sizeof(int64_t) * (size_t)(L.n + 1), cudaMemcpyDeviceToHost));
+  if (col) GMG_CK(cudaMemcpy(col, L.csr_col, sizeof(int32_t) * (size_t)L.nnz, cudaMemcpyDeviceToHost));
+  if (val) GMG_CK(cudaMemcpy(val, L.csr_val, sizeof(double) * (size_t)L.nnz, cudaMemcpyDeviceToHost));
+  if (color) std::copy(L.h_color.begin(), L.h_color.end(), color);
+  return GMG_OK;
+}
+
+// ---- single steps of Alg. 2 (device vectors, caller numbering) ----
+
+static gmg_status to_level(gmg_ctx* c, int l, int fp32, const double* src, double* d64, float* d32,
+                           cudaStream_t s) {
+  GMG_TRY(launch_gather(c->L[l].n, c->L[l].perm, src, d64, s));
+  if (fp32) GMG_TRY(launch_d2f(c->L[l].n, d64, d32, s));
+  return GMG_OK;
+}
+static gmg_status from_level(gmg_ctx* c, int l, int fp32, double* d64, const float* d32, double* dst,
+                             cudaStream_t s) {
+  if (fp32) GMG_TRY(launch_f2d(c->L[l].n, d32, d64, s));
+  return launch_scatter(c->L[l].n, c->L[l].perm, d64, dst, s);
+}
+
+gmg_status gmg_smooth(gmg_handle h, int l, int fp32, const double* b, double* x, int nsweep, int descending,
+                      void* stream) {
+  GMG_TRY(check_handle(h));
+  if (l < 0 || l >= h->nlev || !b || !x || nsweep < 0) return GMG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Level& L = h->L[l];
+  GMG_TRY(to_level(h, l, fp32, b, L.b64, L.b32, s));
+  GMG_TRY(to_level(h, l, fp32, x, L.x64, L.x32, s));
+  for (int it = 0; it < nsweep; ++it)
+    for (int q = 0; q < L.ncolor; ++q) {
+      const int k = descending ? L.ncolor - 1 - q : q;
+      if (fp32) GMG_TRY(launch_gs_colour<float>(L, k, L.b32, L.x32, s));
+      else GMG_TRY(launch_gs_colour<double>(L, k, L.b64, L.x64, s));
+    }
+  return from_level(h, l, fp32, L.x64, L.x32, x, s);
+}
+
+gmg_status gmg_residual(gmg_handle h, int l, int fp32, const double* x, const double* b, double* r, void* stream) {
+  GMG_TRY(check_handle(h));
+  if (l < 0 || l >= h->nlev || !b || !x || !r) return GMG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Level& L = h->L[l];
+  GMG_TRY(to_level(h, l, fp32, b, L.b64, L.b32, s));
+  GMG_TRY(to_level(h, l, fp32, x, L.x64, L.x32, s));
+  if (fp32) GMG_TRY(launch_residual<float>(L, L.x32, L.b32, L.r32, s));
+  else GMG_TRY(launch_residual<double>(L, L.x64, L.b64, L.r64, s));
+  return from_level(h, l, fp32, L.r64, L.r32, r, s);
+}
+
+gmg_status gmg_restrict(gmg_handle h, int l, int fp32, const double* r, double* bc, void* stream) {
+  GMG_TRY(check_handle(h));
+  if (l < 0 || l + 1 >= h->nlev || !r || !bc) return GMG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Level& L = h->L[l];
+  Level& C = h->L[l + 1];
+  GMG_TRY(to_level(h, l, fp32, r, L.r64, L.r32, s));
+  if (fp32) GMG_TRY(launch_restrict<float>(L, L.r32, C.b32, s));
+  else GMG_TRY(launch_restrict<double>(L, L.r64, C.b64, s));
+  return from_level(h, l + 1, fp32, C.b64, C.b32, bc, s);
+}
+
+gmg_status gmg_prolong_add(gmg_handle h, int l, int fp32, const double* u, double* x, void* stream) {
+  GMG_TRY(check_handle(h));
+  if (l < 0 || l + 1 >= h->nlev || !u || !x) return GMG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Level& L = h->L[l];
+  Level& C = h->L[l + 1];
+  GMG_TRY(to_level(h, l + 1, fp32, u, C.x64, C.x32, s));
+  GMG_TRY(to_level(h, l, fp32, x, L.x64, L.x32, s));
+  if (fp32) GMG_TRY(launch_prolong<float>(L, C.x32, L.x32, s));
+  else GMG_TRY(launch_prolong<double>(L, C.x64, L.x64, s));
+  return from_level(h, l, fp32, L.x64, L.x32, x, s);
+}
+
+gmg_status gmg_coarse_solve(gmg_handle h, int fp32, const double* b, double* x, void* stream) {
+  GMG_TRY(check_handle(h));
+  if (!b || !x) return GMG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int l = h->nlev - 1;
+  Level& C = h->L[l];
+  GMG_TRY(to_level(h, l, fp32, b, C.b64, C.b32, s));
+  if (fp32) GMG_TRY(launch_coarse<float>(h, C.b32, C.x32, s));
+  else GMG_TRY(launch_coarse<double>(h, C.b64, C.x64, s));
+  return from_level(h, l, fp32, C.x64, C.x32, x, s);
+}
+
+gmg_status gmg_vcycle(gmg_handle h, int fp32, const double* b, double* x, void* stream) {
+  GMG_TRY(check_handle(h));
+  if (!b || !x) return GMG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Level& L = h->L[0];
+  GMG_TRY(to_level(h, 0, fp32, b, L.b64, L.b32, s));
+  GMG_TRY(to_level(h, 0, fp32, x, L.x64, L.x32, s));
+  if (fp32) GMG_TRY(vcycle<float>(h, 0, false, s));
+  else GMG_TRY(vcycle<double>(h, 0, false, s));
+  return from_level(h, 0, fp32, L.x64, L.x32, x, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,466 @@
+// Many right-hand sides at once (SpMM-style V-cycle): every level's vectors
+// are [n_l x NR] row-major in the permuted numbering, so each matrix entry is
+// read once and applied to NR contiguous values (NR = 1, 2, 4, 8 or 16; the
+// caller's nrhs is padded with zero columns).  The inner cycle runs in FP32
+// (coarsest solve in FP64) inside FP64 iterative refinement, as in Alg. 1
+// with the correction form x += MGI(0, b - A x).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "gmg_cycle.cuh"
+
+namespace gmg {
+
+template <int NR>
+struct alignas(16) Row {
+  float v[NR];
+};
+
+template <int NR>
+__device__ __forceinline__ void load_row(const float* __restrict__ p, float (&o)[NR]) {
+  if constexpr (NR % 4 == 0) {
+#pragma unroll
+    for (int c = 0; c < NR; c += 4) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(p + c));
+      o[c] = q.x;
+      o[c + 1] = q.y;
+      o[c + 2] = q.z;
+      o[c + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NR; ++c) o[c] = __ldg(p + c);
+  }
+}
+
+template <int NR>
+__device__ __forceinline__ void store_row(float* __restrict__ p, const float (&o)[NR]) {
+  if constexpr (NR % 4 == 0) {
+#pragma unroll
+    for (int c = 0; c < NR; c += 4) *reinterpret_cast<float4*>(p + c) = make_float4(o[c], o[c + 1], o[c + 2], o[c + 3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < NR; ++c) p[c] = o[c];
+  }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) k_gs_m(int64_t s0, int64_t s1, const int64_t* __restrict__ ptr,
+                                              const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
+                                              const int32_t* __restrict__ col, const float* __restrict__ val,
+                                              const float* __restrict__ dinv, const float* __restrict__ B, float* X) {
+  const int64_t s = s0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= s1 || lane >= nrow[s]) return;
+  const int64_t r = row0[s] + lane;
+  const int64_t e0 = ptr[s];
+  const int w = (int)((ptr[s + 1] - e0) >> 5);
+  float acc[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = 0.f;
+  int64_t e = e0 + lane;
+  for (int k = 0; k < w; ++k, e += 32) {
+    const float a = val[e];
+    float xv[NR];
+    load_row<NR>(X + (int64_t)col[e] * NR, xv);  // other colours: not written by this launch
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[c] += a * xv[c];
+  }
+  float bv[NR];
+  load_row<NR>(B + r * NR, bv);
+  const float d = dinv[r];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = (bv[c] - acc[c]) * d;
+  store_row<NR>(X + r * NR, acc);
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) k_residual_m(int64_t nslice, const int64_t* __restrict__ ptr,
+                                                    const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
+                                                    const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                    const float* __restrict__ diag, const float* __restrict__ X,
+                                                    const float* __restrict__ B, float* __restrict__ R) {
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= nslice || lane >= nrow[s]) return;
+  const int64_t r = row0[s] + lane;
+  const int64_t e0 = ptr[s];
+  const int w = (int)((ptr[s + 1] - e0) >> 5);
+  float acc[NR], xv[NR];
+  load_row<NR>(X + r * NR, xv);
+  const float d = diag[r];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = d * xv[c];
+  int64_t e = e0 + lane;
+  for (int k = 0; k < w; ++k, e += 32) {
+    const float a = val[e];
+    load_row<NR>(X + (int64_t)col[e] * NR, xv);
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[c] += a * xv[c];
+  }
+  float bv[NR];
+  load_row<NR>(B + r * NR, bv);
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = bv[c] - acc[c];
+  store_row<NR>(R + r * NR, acc);
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) k_restrict_m(int64_t nslice, const int64_t* __restrict__ ptr,
+                                                    const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
+                                                    const int32_t* __restrict__ col, const float* __restrict__ w,
+                                                    const float* __restrict__ R, float* __restrict__ Bc) {
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= nslice || lane >= nrow[s]) return;
+  const int64_t e0 = ptr[s];
+  const int wd = (int)((ptr[s + 1] - e0) >> 5);
+  float acc[NR], rv[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = 0.f;
+  int64_t e = e0 + lane;
+  for (int k = 0; k < wd; ++k, e += 32) {
+    const float a = w[e];
+    load_row<NR>(R + (int64_t)col[e] * NR, rv);
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[c] += a * rv[c];
+  }
+  store_row<NR>(Bc + (int64_t)(row0[s] + lane) * NR, acc);
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) k_prolong_m(int64_t n, const int32_t* __restrict__ idx,
+                                                   const float* __restrict__ w, const float* __restrict__ U,
+                                                   float* __restrict__ X) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float xv[NR], u[NR];
+    load_row<NR>(X + i * NR, xv);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const float a = w[3 * i + m];
+      load_row<NR>(U + (int64_t)idx[3 * i + m] * NR, u);
+#pragma unroll
+      for (int c = 0; c < NR; ++c) xv[c] += a * u[c];
+    }
+    store_row<NR>(X + i * NR, xv);
+  }
+}
+
+// X = Ainv B on the coarsest level (FP64 accumulation), one warp per row.
+template <int NR>
+__global__ void __launch_bounds__(256) k_coarse_m(int n, const double* __restrict__ Ainv, const float* __restrict__ B,
+                                                  float* __restrict__ X) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double s[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) s[c] = 0.0;
+  const double* a = Ainv + (int64_t)row * n;
+  for (int j = lane; j < n; j += 32) {
+    const double aj = a[j];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) s[c] += aj * (double)B[(int64_t)j * NR + c];
+  }
+#pragma unroll
+  for (int c = 0; c < NR; ++c)
+    for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) X[(int64_t)row * NR + c] = (float)s[c];
+}
+
+// FP64 outer residual R = B - A X with per-block, per-column partial sums of
+// R^2 (fixed-shape reduction), and the correction cast R32 = (float) R.
+template <int NR>
+__global__ void __launch_bounds__(256) k_outer_residual_m(int64_t nslice, const int64_t* __restrict__ ptr,
+                                                          const int32_t* __restrict__ row0,
+                                                          const int32_t* __restrict__ nrow,
+                                                          const int32_t* __restrict__ col,
+                                                          const double* __restrict__ val,
+                                                          const double* __restrict__ diag,
+                                                          const double* __restrict__ X, const double* __restrict__ B,
+                                                          float* __restrict__ R32, double* __restrict__ partial) {
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  double sq[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) sq[c] = 0.0;
+  if (s < nslice && lane < nrow[s]) {
+    const int64_t r = row0[s] + lane;
+    const int64_t e0 = ptr[s];
+    const int w = (int)((ptr[s + 1] - e0) >> 5);
+    double acc[NR];
+    const double d = diag[r];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[c] = d * X[r * NR + c];
+    int64_t e = e0 + lane;
+    for (int k = 0; k < w; ++k, e += 32) {
+      const double a = val[e];
+      const double* xj = X + (int64_t)col[e] * NR;
+#pragma unroll
+      for (int c = 0; c < NR; ++c) acc[c] += a * xj[c];
+    }
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const double rv = B[r * NR + c] - acc[c];
+      R32[r * NR + c] = (float)rv;
+      sq[c] = rv * rv;
+    }
+  }
+  __shared__ double red[NR][256];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) red[c][threadIdx.x] = sq[c];
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+#pragma unroll
+      for (int c = 0; c < NR; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < NR) partial[(int64_t)blockIdx.x * NR + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// out[c] = sum over blocks of partial[b * NR + c] (fixed order).
+__global__ void k_reduce_cols(int nblocks, int nr, const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double red[256];
+  for (int c = 0; c < nr; ++c) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 256) s += partial[(int64_t)b * nr + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = red[0];
+    __syncthreads();
+  }
+}
+
+// Caller [n x nrhs] (double) -> permuted [n x NR] with zero padding, and back.
+__global__ void k_gather_m(int64_t n, int nrhs, int NR, const int32_t* __restrict__ perm, const double* __restrict__ src,
+                           double* __restrict__ dst) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * NR; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / NR;
+    const int c = (int)(t % NR);
+    dst[t] = c < nrhs ? src[(int64_t)perm[i] * nrhs + c] : 0.0;
+  }
+}
+__global__ void k_scatter_m(int64_t n, int nrhs, int NR, const int32_t* __restrict__ perm,
+                            const double* __restrict__ src, double* __restrict__ dst) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * nrhs;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / nrhs;
+    const int c = (int)(t % nrhs);
+    dst[(int64_t)perm[i] * nrhs + c] = src[i * NR + c];
+  }
+}
+__global__ void k_zero_cols(int64_t n, int NR, int mask, double* __restrict__ X) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * NR; t += (int64_t)gridDim.x * blockDim.x)
+    if ((mask >> (int)(t % NR)) & 1) X[t] = 0.0;
+}
+__global__ void k_add_f2d_m(int64_t m, const float* __restrict__ e, double* __restrict__ x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)e[i];
+}
+
+static inline int nblk(int64_t threads) { return (int)std::max<int64_t>(1, (threads + 255) / 256); }
+static inline int gblk(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 64)); }
+
+#define LCK() GMG_LAUNCHED()
+
+template <int NR>
+static gmg_status vcycle_m(gmg_ctx* c, int l, cudaStream_t s) {
+  Level& L = c->L[l];
+  if (l == c->nlev - 1) {
+    k_coarse_m<NR><<<(int)((L.n * 32 + 255) / 256), 256, 0, s>>>((int)L.n, c->Ainv, L.B32, L.X32);
+    LCK();
+    return GMG_OK;
+  }
+  Level& C = c->L[l + 1];
+  GMG_CK(cudaMemsetAsync(L.X32, 0, sizeof(float) * (size_t)(L.n * NR), s));
+  auto sweep = [&](int k) -> gmg_status {
+    const int64_t s0 = L.color_slice_off[k], s1 = L.color_slice_off[k + 1];
+    if (s1 > s0)
+      k_gs_m<NR><<<nblk((s1 - s0) * 32), 256, 0, s>>>(s0, s1, L.A.ptr, L.A.row0, L.A.nrow, L.A.col, L.A.v32,
+                                                     L.dinv32, L.B32, L.X32);
+    LCK();
+    return GMG_OK;
+  };
+  for (int it = 0; it < c->opt.nu_pre; ++it)
+    for (int k = 0; k < L.ncolor; ++k) GMG_TRY(sweep(k));
+  k_residual_m<NR><<<nblk(L.A.nslice * 32), 256, 0, s>>>(L.A.nslice, L.A.ptr, L.A.row0, L.A.nrow, L.A.col, L.A.v32,
+                                                        L.diag32, L.X32, L.B32, L.R32);
+  LCK();
+  k_restrict_m<NR><<<nblk(L.R.nslice * 32), 256, 0, s>>>(L.R.nslice, L.R.ptr, L.R.row0, L.R.nrow, L.R.col, L.R.v32,
+                                                        L.R32, C.B32);
+  LCK();
+  GMG_TRY(vcycle_m<NR>(c, l + 1, s));
+  k_prolong_m<NR><<<gblk(L.n), 256, 0, s>>>(L.n, L.p_idx, L.p_w32, C.X32, L.X32);
+  LCK();
+  for (int it = 0; it < c->opt.nu_post; ++it)
+    for (int q = 0; q < L.ncolor; ++q) GMG_TRY(sweep(c->opt.post_forward ? q : L.ncolor - 1 - q));
+  return GMG_OK;
+}
+
+// R = B - A X (FP64) -> level-0 B32 and per-column ||R||^2 into scal[8 + c].
+template <int NR>
+static gmg_status outer_m(gmg_ctx* c, cudaStream_t s) {
+  Level& L = c->L[0];
+  const int nb = nblk(L.A.nslice * 32);
+  k_outer_residual_m<NR><<<nb, 256, 0, s>>>(L.A.nslice, L.A.ptr, L.A.row0, L.A.nrow, L.A.col, L.A.v64, L.diag64,
+                                           c->XS, c->BS, L.B32, c->red);
+  LCK();
+  k_reduce_cols<<<1, 256, 0, s>>>(nb, NR, c->red, c->scal + 8);
+  LCK();
+  return GMG_OK;
+}
+
+template <int NR>
+static gmg_status iteration_m(gmg_ctx* c, cudaStream_t s) {
+  Level& L = c->L[0];
+  GMG_TRY(vcycle_m<NR>(c, 0, s));
+  k_add_f2d_m<<<gblk(L.n * NR), 256, 0, s>>>(L.n * NR, L.X32, c->XS);
+  LCK();
+  return outer_m<NR>(c, s);
+}
+
+static gmg_status ensure_batched(gmg_ctx* c) {
+  if (c->XS) return GMG_OK;
+  for (auto& L : c->L) {
+    GMG_TRY(c->arena.alloc(&L.X32, (size_t)L.n * kMaxRhs));
+    GMG_TRY(c->arena.alloc(&L.B32, (size_t)L.n * kMaxRhs));
+    GMG_TRY(c->arena.alloc(&L.R32, (size_t)L.n * kMaxRhs));
+  }
+  const int64_t n = c->L[0].n;
+  GMG_TRY(c->arena.alloc(&c->XS, (size_t)n * kMaxRhs));
+  GMG_TRY(c->arena.alloc(&c->BS, (size_t)n * kMaxRhs));
+  GMG_TRY(c->arena.alloc(&c->RS, (size_t)n * kMaxRhs));
+  const int64_t need = (int64_t)nblk(c->L[0].A.nslice * 32) * kMaxRhs + 64;
+  double* red2;
+  GMG_TRY(c->arena.alloc(&red2, (size_t)std::max<int64_t>(need, 4 * kRedBlocks)));
+  c->red = red2;
+  return GMG_OK;
+}
+
+template <int NR>
+static gmg_status solve_m(gmg_ctx* c, int nrhs, const double* B, double* X, double tol, int mem,
+                          gmg_solve_info* info, cudaStream_t s) {
+  Level& L0 = c->L[0];
+  const int64_t n = L0.n;
+  const size_t bytes = sizeof(double) * (size_t)(n * nrhs);
+  const double* bsrc = B;
+  const double* xsrc = X;
+  if (mem == GMG_MEM_HOST) {
+    GMG_CK(cudaMemcpyAsync(c->RS, B, bytes, cudaMemcpyHostToDevice, s));
+    bsrc = c->RS;
+  }
+  k_gather_m<<<gblk(n * NR), 256, 0, s>>>(n, nrhs, NR, L0.perm, bsrc, c->BS);
+  LCK();
+  if (mem == GMG_MEM_HOST) {
+    GMG_CK(cudaMemcpyAsync(c->RS, X, bytes, cudaMemcpyHostToDevice, s));
+    xsrc = c->RS;
+  }
+  k_gather_m<<<gblk(n * NR), 256, 0, s>>>(n, nrhs, NR, L0.perm, xsrc, c->XS);
+  LCK();
+  // column norms of B: the outer residual with X = 0 (RS as a zero iterate)
+  GMG_CK(cudaMemsetAsync(c->scal, 0, 64 * sizeof(double), s));
+  double nb[kMaxRhs];
+  bool all_zero = true;
+  {
+    double* keep = c->XS;
+    c->XS = c->RS;
+    GMG_CK(cudaMemsetAsync(c->RS, 0, sizeof(double) * (size_t)(n * NR), s));
+    GMG_TRY(outer_m<NR>(c, s));
+    c->XS = keep;
+    GMG_CK(cudaMemcpyAsync(c->h_scal + 8, c->scal + 8, NR * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GMG_CK(cudaStreamSynchronize(s));
+    int zmask = 0;
+    for (int q = 0; q < nrhs; ++q) {
+      nb[q] = std::sqrt(c->h_scal[8 + q]);
+      if (nb[q] == 0.0) zmask |= 1 << q;
+      else all_zero = false;
+    }
+    if (zmask) {  // a zero right-hand side has the solution 0
+      k_zero_cols<<<gblk(n * NR), 256, 0, s>>>(n, NR, zmask, c->XS);
+      LCK();
+    }
+  }
+  auto worst = [&]() {
+    double w = 0.0;
+    for (int q = 0; q < nrhs; ++q) {
+      const double r = nb[q] > 0 ? std::sqrt(c->h_scal[8 + q]) / nb[q] : 0.0;
+      if (!std::isfinite(r)) return r;
+      w = std::max(w, r);
+    }
+    return w;
+  };
+  GMG_TRY(outer_m<NR>(c, s));
+  GMG_CK(cudaMemcpyAsync(c->h_scal + 8, c->scal + 8, NR * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GMG_CK(cudaStreamSynchronize(s));
+  double rel = worst();
+  if (info && info->history && info->history_cap > 0) info->history[0] = rel;
+  gmg_status st = GMG_ERR_NOT_CONVERGED;
+  int k = 0;
+  if (!std::isfinite(rel)) {
+    st = GMG_ERR_NONFINITE;
+  } else if (all_zero) {
+    st = GMG_OK;
+  } else {
+    while (k < c->opt.max_iter) {
+      GMG_TRY(iteration_m<NR>(c, s));
+      GMG_CK(cudaMemcpyAsync(c->h_scal + 8, c->scal + 8, NR * sizeof(double), cudaMemcpyDeviceToHost, s));
+      GMG_CK(cudaStreamSynchronize(s));
+      ++k;
+      rel = worst();
+      if (info && info->history && k < info->history_cap) info->history[k] = rel;
+      if (!std::isfinite(rel)) {
+        st = GMG_ERR_NONFINITE;
+        break;
+      }
+      if (rel <= tol) {
+        st = GMG_OK;
+        break;
+      }
+    }
+  }
+  double* dst = mem == GMG_MEM_HOST ? c->RS : X;
+  k_scatter_m<<<gblk(n * nrhs), 256, 0, s>>>(n, nrhs, NR, L0.perm, c->XS, dst);
+  LCK();
+  if (mem == GMG_MEM_HOST) {
+    GMG_CK(cudaMemcpyAsync(X, c->RS, bytes, cudaMemcpyDeviceToHost, s));
+    GMG_CK(cudaStreamSynchronize(s));
+  }
+  if (info) {
+    info->iters = k;
+    info->rel_res = rel;
+  }
+  if (st == GMG_ERR_NOT_CONVERGED) set_error("gmg_solve_batched: max_iter reached");
+  if (st == GMG_ERR_NONFINITE) set_error("gmg_solve_batched: non-finite residual");
+  return st;
+}
+
+}  // namespace gmg
+
+using namespace gmg;
+
+extern "C" gmg_status gmg_solve_batched(gmg_handle h, int nrhs, const double* B, double* X, double tol, int mem,
+                                        gmg_solve_info* info, void* stream) {
+  if (!h || !B || !X || nrhs < 1 || nrhs > kMaxRhs || !(tol >= 0.0) ||
+      (mem != GMG_MEM_HOST && mem != GMG_MEM_DEVICE)) {
+    set_error("gmg_solve_batched: bad handle, vector, nrhs (1..16), tolerance or memory kind");
+    return GMG_ERR_INVALID_ARG;
+  }
+  GMG_CK(cudaSetDevice(h->device));
+  GMG_TRY(ensure_batched(h));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nrhs == 1) return solve_m<1>(h, nrhs, B, X, tol, mem, info, s);
+  if (nrhs == 2) return solve_m<2>(h, nrhs, B, X, tol, mem, info, s);
+  if (nrhs <= 4) return solve_m<4>(h, nrhs, B, X, tol, mem, info, s);
+  if (nrhs <= 8) return solve_m<8>(h, nrhs, B, X, tol, mem, info, s);
+  return solve_m<16>(h, nrhs, B, X, tol, mem, info, s);
+}

@@ -1,0 +1,50 @@
+// Solve-phase kernels of the V-cycle (Alg. 2) shared by the single- and
+// multi-right-hand-side paths.
+#pragma once
+#include "gmg_internal.cuh"
+
+namespace gmg {
+
+gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s);
+gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P, cudaStream_t s);
+
+// level-vector selection by precision
+template <class T> struct Vec;
+template <> struct Vec<double> {
+  static double* x(Level& L) { return L.x64; }
+  static double* b(Level& L) { return L.b64; }
+  static double* r(Level& L) { return L.r64; }
+  static const double* v(const Ell& E) { return E.v64; }
+  static const double* dinv(const Level& L) { return L.dinv64; }
+  static const double* diag(const Level& L) { return L.diag64; }
+  static const double* pw(const Level& L) { return L.p_w64; }
+};
+template <> struct Vec<float> {
+  static float* x(Level& L) { return L.x32; }
+  static float* b(Level& L) { return L.b32; }
+  static float* r(Level& L) { return L.r32; }
+  static const float* v(const Ell& E) { return E.v32; }
+  static const float* dinv(const Level& L) { return L.dinv32; }
+  static const float* diag(const Level& L) { return L.diag32; }
+  static const float* pw(const Level& L) { return L.p_w32; }
+};
+
+// host launchers (gmg_cycle.cu)
+template <class T> gmg_status launch_gs_colour(Level& L, int colour, const T* b, T* x, cudaStream_t s);
+template <class T> gmg_status launch_residual(Level& L, const T* x, const T* b, T* r, cudaStream_t s);
+template <class T> gmg_status launch_restrict(Level& L, const T* r, T* bc, cudaStream_t s);
+template <class T> gmg_status launch_prolong(Level& L, const T* u, T* x, cudaStream_t s);
+template <class T> gmg_status launch_coarse(gmg_ctx* c, const T* b, T* x, cudaStream_t s);
+template <class T> gmg_status vcycle(gmg_ctx* c, int l, bool zero_x, cudaStream_t s);
+
+gmg_status launch_d2f(int64_t n, const double* a, float* b, cudaStream_t s);
+gmg_status launch_f2d(int64_t n, const float* a, double* b, cudaStream_t s);
+gmg_status iteration_body(gmg_ctx* c, int mode, int seg, cudaStream_t s);
+gmg_status pcg_start(gmg_ctx* c, cudaStream_t s);
+gmg_status outer_residual_norm(gmg_ctx* c, cudaStream_t s);
+gmg_status norm_b(gmg_ctx* c, cudaStream_t s);
+enum { S_NB2 = 0, S_RR = 1, S_RZ = 2, S_PQ = 3, S_NUM = 4, S_RZN = 5 };
+gmg_status launch_gather(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t s);
+gmg_status launch_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t s);
+
+}  // namespace gmg

@@ -1,0 +1,232 @@
+"""GPU parity: every step of Alg. 2, whole V-cycles and whole solves of the
+CUDA library against the CPU FP64 oracle, through the C ABI.
+
+Tolerances (normwise relative, ||gpu - oracle|| / ||oracle||):
+  * FP64 steps and FP64 V-cycles: 1e-12 (only the summation order, the
+    reciprocal diagonal and the explicit coarse inverse differ);
+  * FP32 steps and FP32 V-cycles: 1e-6 (inputs rounded to FP32, about
+    6e-8 relative, amplified by a few operator applications);
+  * solves: both sides reach ||b - A x|| <= 1e-10 ||b||; the solutions agree
+    to 1e-8 relative (the residual bound times the system's condition).
+Integer results (Galerkin patterns, colourings) must be identical.
+"""
+import numpy as np
+import pytest
+
+import gmg_inputs as gi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+SEED = 1234
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def gmg(cuda):
+    import paper_2307_04886_gb300 as g
+
+    g.load_library()
+    return g
+
+
+def _systems():
+    return {
+        "icosphere5": lambda: gi.icosphere_system(5),
+        "torus256x120": lambda: gi.torus_system(256, 120, 1e-4, 7),
+    }
+
+
+@pytest.fixture(scope="module", params=["icosphere5", "torus256x120"])
+def pair(request, gmg):
+    s = _systems()[request.param]()
+    o = oracle.Oracle(s.A, s.Ps)
+    g = gmg.Solver(s.A, s.Ps)
+    yield s, o, g
+    g.close()
+
+
+def _t(x):
+    import torch
+
+    return torch.tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def test_levels_and_colourings_match(pair):
+    s, o, g = pair
+    assert g.nlev == o.nlev
+    for l in range(o.nlev):
+        Ao, co = o.level(l)
+        Ag, cg = g.level(l)
+        assert np.array_equal(Ao.indptr, Ag.indptr) and np.array_equal(Ao.indices, Ag.indices), f"pattern of level {l}"
+        assert np.array_equal(co, cg), f"colouring of level {l}"
+        assert rel(Ag.data, Ao.data) <= 1e-13, f"values of level {l}"
+        d = Ag - Ag.T
+        assert abs(d).max() == 0.0, "Galerkin operator must be exactly symmetric"
+
+
+@pytest.mark.parametrize("fp32,tol", [(False, 1e-12), (True, 1e-6)])
+def test_steps_match(pair, fp32, tol):
+    s, o, g = pair
+    rng = np.random.default_rng(SEED)
+    for l in range(o.nlev - 1):
+        n, nc = o.n(l), o.n(l + 1)
+        x, b, u = rng.standard_normal(n), rng.standard_normal(n), rng.standard_normal(nc)
+        for desc in (False, True):
+            xo = o.smooth(l, x, b, 2, desc)
+            xg = _np(g.smooth(l, _t(x), _t(b), 2, desc, fp32=fp32))
+            assert rel(xg, xo) <= tol, f"smooth level {l} desc={desc}"
+        ro = o.residual(l, x, b)
+        rg = _np(g.residual(l, _t(x), _t(b), _t(np.zeros(n)), fp32=fp32))
+        assert rel(rg, ro) <= tol * 10, f"residual level {l}"
+        bo = o.restrict(l, b)
+        bg = _np(g.restrict(l, _t(b), _t(np.zeros(nc)), fp32=fp32))
+        assert rel(bg, bo) <= tol, f"restrict level {l}"
+        po = o.prolong_add(l, u, x)
+        pg = _np(g.prolong_add(l, _t(u), _t(x), fp32=fp32))
+        assert rel(pg, po) <= tol, f"prolong level {l}"
+    nl = o.n(o.nlev - 1)
+    b = rng.standard_normal(nl)
+    co = o.coarse_solve(b)
+    cg = _np(g.coarse_solve(_t(b), _t(np.zeros(nl)), fp32=fp32))
+    assert rel(cg, co) <= max(tol, 1e-11), "coarse solve"
+
+
+@pytest.mark.parametrize("fp32,tol", [(False, 1e-12), (True, 1e-6)])
+def test_vcycle_matches(pair, fp32, tol):
+    s, o, g = pair
+    rng = np.random.default_rng(SEED + 1)
+    x0 = rng.standard_normal(s.n)
+    b = s.b
+    xo = o.vcycle(x0, b)
+    xg = _np(g.vcycle(_t(x0), _t(b), fp32=fp32))
+    assert rel(xg, xo) <= tol
+    # a second cycle from the first one's output
+    xo2 = o.vcycle(xo, b)
+    xg2 = _np(g.vcycle(_t(xg), _t(b), fp32=fp32))
+    assert rel(xg2, xo2) <= tol
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_solve_matches(gmg, precision):
+    s = gi.icosphere_system(5)
+    o = oracle.Oracle(s.A, s.Ps)
+    xo, ito, ho, ok = o.solve(s.b, tol=1e-10, pcg=precision == 2)
+    assert ok
+    g = gmg.Solver(s.A, s.Ps, precision=precision)
+    xg, it, rr, hist, st = g.solve(_t(s.b), tol=1e-10, history=101)
+    xg = _np(xg)
+    true_rel = np.linalg.norm(s.b - s.A @ xg) / np.linalg.norm(s.b)
+    assert true_rel <= 1e-10
+    assert abs(true_rel - rr) <= 1e-12
+    assert rel(xg, xo) <= 1e-8
+    if precision == 0:
+        assert it == ito
+        assert np.allclose(hist, ho, rtol=1e-6, atol=0)
+    else:
+        assert abs(it - ito) <= 2
+    g.close()
+
+
+def test_host_and_device_paths_agree(gmg):
+    s = gi.icosphere_system(4)
+    g = gmg.Solver(s.A, s.Ps)
+    xd, itd, _, _, _ = g.solve(_t(s.b), tol=1e-10)
+    xh, ith, _, _, _ = g.solve(np.asarray(s.b), tol=1e-10)
+    assert itd == ith
+    assert np.array_equal(_np(xd), xh)
+    g.close()
+
+
+def test_deterministic(gmg):
+    s = gi.torus_system(128, 64, 1e-4, 3)
+    g = gmg.Solver(s.A, s.Ps)
+    x1 = _np(g.solve(_t(s.b), tol=1e-10)[0])
+    x2 = _np(g.solve(_t(s.b), tol=1e-10)[0])
+    assert np.array_equal(x1, x2)
+    g2 = gmg.Solver(s.A, s.Ps)
+    x3 = _np(g2.solve(_t(s.b), tol=1e-10)[0])
+    assert np.array_equal(x1, x3)
+    g.close()
+    g2.close()
+
+
+def test_zero_rhs(gmg):
+    s = gi.icosphere_system(3)
+    g = gmg.Solver(s.A, s.Ps)
+    x, it, rr, _, st = g.solve(_t(np.zeros(s.n)), _t(np.ones(s.n)), tol=1e-10)
+    assert it == 0 and st == 0
+    assert float(abs(x).max()) == 0.0
+    g.close()
+
+
+def test_single_level_is_direct_solve(gmg):
+    s = gi.icosphere_system(2)  # 162 vertices: no coarsening needed
+    g = gmg.Solver(s.A, [])
+    assert g.nlev == 1
+    x, it, rr, _, st = g.solve(_t(s.b), tol=1e-10)
+    assert it == 1 and rr <= 1e-12
+    import scipy.sparse.linalg as sla
+
+    assert rel(_np(x), sla.spsolve(s.A.tocsc(), s.b)) <= 1e-12
+    g.close()
+
+
+def test_set_values_refresh(gmg):
+    s = gi.icosphere_system(4)
+    g = gmg.Solver(s.A, s.Ps)
+    import scipy.sparse as sp
+
+    A3 = (sp.diags(s.Mdiag) + 3e-3 * s.L).tocsr()
+    A3.sort_indices()
+    assert np.array_equal(A3.indices, s.A.indices)
+    g.set_values(A3.data)
+    o = oracle.Oracle(A3, s.Ps)
+    for l in range(o.nlev):
+        assert rel(g.level(l)[0].data, o.level(l)[0].data) <= 1e-13
+    x, it, rr, _, _ = g.solve(_t(s.b), tol=1e-10)
+    assert np.linalg.norm(s.b - A3 @ _np(x)) / np.linalg.norm(s.b) <= 1e-10
+    g.close()
+
+
+def test_batched_matches_single(gmg):
+    s = gi.icosphere_system(5)
+    rng = np.random.default_rng(SEED + 2)
+    for nrhs in (1, 3, 8):
+        B = rng.standard_normal((s.n, nrhs)) * s.Mdiag[:, None]
+        g = gmg.Solver(s.A, s.Ps)
+        X, it, rr, _, st = g.solve_batched(_t(B), tol=1e-10)
+        X = _np(X)
+        for c in range(nrhs):
+            r = np.linalg.norm(B[:, c] - s.A @ X[:, c]) / np.linalg.norm(B[:, c])
+            assert r <= 1e-10
+            xs = _np(g.solve(_t(B[:, c].copy()), tol=1e-10)[0])
+            assert rel(X[:, c], xs) <= 1e-8
+        g.close()
+
+
+@pytest.mark.slow
+def test_full_size_torus(gmg):
+    """The 1M-vertex torus in the launch configuration the bench times:
+    FP32 V-cycle parity on the full system and a solve to 1e-10."""
+    s = gi.workload("torus1m")
+    o = oracle.Oracle(s.A, s.Ps)
+    g = gmg.Solver(s.A, s.Ps, precision=1)
+    for l in range(o.nlev):
+        Ao, co = o.level(l)
+        Ag, cg = g.level(l)
+        assert np.array_equal(Ao.indices, Ag.indices) and np.array_equal(co, cg)
+        assert rel(Ag.data, Ao.data) <= 1e-13
+    xo = o.vcycle(np.zeros(s.n), s.b)
+    xg = _np(g.vcycle(_t(np.zeros(s.n)), _t(s.b), fp32=True))
+    assert rel(xg, xo) <= 1e-6
+    x, it, rr, _, _ = g.solve(_t(s.b), tol=1e-10)
+    assert np.linalg.norm(s.b - s.A @ _np(x)) / np.linalg.norm(s.b) <= 1e-10
+    g.close()
