@@ -269,16 +269,23 @@ __global__ void k_scatter_values(int64_t nnz, const int64_t* __restrict__ csr2el
   }
 }
 
+// Dense coarsest operator in the level's colour-permuted numbering (the
+// numbering of the vectors the cycle hands to the coarse solve).
 __global__ void k_csr_to_dense(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                               const double* __restrict__ val, double* __restrict__ D) {
-  for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
-    for (int64_t k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x) D[i * n + col[k]] = val[k];
+                               const double* __restrict__ val, const int32_t* __restrict__ iperm,
+                               double* __restrict__ D) {
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const int64_t pi = iperm[i];
+    for (int64_t k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x) D[pi * n + iperm[col[k]]] = val[k];
+  }
 }
 
 // ---- dense FP64 Cholesky, right-looking, 32 x 32 blocks ----
-// Factors the diagonal block p (redundantly in every CTA's shared memory) and
-// solves the rows below it: L_ip = A_ip L_pp^-T.  status bit 0: pivot <= 0.
-__global__ void k_chol_panel(int n, int p, double* __restrict__ A, int* __restrict__ status) {
+// k_chol_diag (one CTA) factors the diagonal block p in shared memory and
+// writes L_pp back; k_chol_panel then solves the rows below it,
+// L_ip = A_ip L_pp^-T; k_chol_update applies the trailing update.
+// status bit 0: a pivot <= 0.
+__global__ void k_chol_diag(int n, int p, double* __restrict__ A, int* __restrict__ status) {
   __shared__ double D[32][33];
   __shared__ int bad;
   const int j0 = p * 32;
@@ -308,12 +315,21 @@ __global__ void k_chol_panel(int n, int p, double* __restrict__ A, int* __restri
     __syncthreads();
   }
   if (bad && threadIdx.x == 0) atomicOr(status, 1);
-  if (blockIdx.x == 0) {
-    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-      const int r = idx >> 5, c = idx & 31;
-      if (r < nb && c < nb) A[(int64_t)(j0 + r) * n + j0 + c] = (c <= r) ? D[r][c] : 0.0;
-    }
+  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+    const int r = idx >> 5, c = idx & 31;
+    if (r < nb && c < nb) A[(int64_t)(j0 + r) * n + j0 + c] = (c <= r) ? D[r][c] : 0.0;
   }
+}
+
+__global__ void k_chol_panel(int n, int p, double* __restrict__ A) {
+  __shared__ double D[32][33];
+  const int j0 = p * 32;
+  const int nb = min(32, n - j0);
+  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+    const int r = idx >> 5, c = idx & 31;
+    D[r][c] = (r < nb && c < nb) ? A[(int64_t)(j0 + r) * n + j0 + c] : (r == c ? 1.0 : 0.0);
+  }
+  __syncthreads();
   const int i = j0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     double v[32];
@@ -708,13 +724,17 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s) {
   Level& C = c->L[c->nlev - 1];
   const int n = (int)c->nco;
   GMG_CK(cudaMemsetAsync(c->dense, 0, sizeof(double) * (size_t)n * n, s));
-  k_csr_to_dense<<<std::min(n, 4096), 128, 0, s>>>(n, C.csr_rowptr, C.csr_col, C.csr_val, c->dense);
+  k_csr_to_dense<<<std::min(n, 4096), 128, 0, s>>>(n, C.csr_rowptr, C.csr_col, C.csr_val, C.iperm, c->dense);
   GMG_LAUNCHED();
   const int nbk = (n + 31) / 32;
   for (int p = 0; p < nbk; ++p) {
     const int below = n - std::min(n, (p + 1) * 32);
-    k_chol_panel<<<std::max(1, (below + 127) / 128), 128, 0, s>>>(n, p, c->dense, c->dstatus + 1);
+    k_chol_diag<<<1, 256, 0, s>>>(n, p, c->dense, c->dstatus + 1);
     GMG_LAUNCHED();
+    if (below > 0) {
+      k_chol_panel<<<(below + 127) / 128, 128, 0, s>>>(n, p, c->dense);
+      GMG_LAUNCHED();
+    }
     const int T = nbk - p - 1;
     if (T > 0) {
       k_chol_update<<<T * (T + 1) / 2, 256, 0, s>>>(n, p, c->dense);
