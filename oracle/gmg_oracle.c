@@ -102,7 +102,7 @@ static int cmp_i32(const void *a, const void *b) {
 }
 
 /* Galerkin coarse operator A_c = P^T A P (Alg. 1, build level matrix).
- * Entry (J, K) = sum_i sum_j P_iJ A_ij P_jK, accumulated for each coarse row J
+ * Entry (J, K) = sum_i sum_j (P_iJ P_jK) A_ij, accumulated for each coarse row J
  * over the fine rows i of column J of P (ascending), the entries j of row i of
  * A (ascending) and the slots of row j of P, then mirrored to exact symmetry. */
 static int galerkin(const olevel *F, olevel *C) {
@@ -151,7 +151,7 @@ static int galerkin(const olevel *F, olevel *C) {
           if (wjK == 0.0) continue;
           int32_t K = F->pidx[3 * j + s];
           if (mark[K] != J) { mark[K] = J; acc[K] = 0.0; touched[nt++] = K; }
-          acc[K] += (wiJ * a) * wjK;
+          acc[K] += (wiJ * wjK) * a;
         }
       }
     }
