@@ -368,8 +368,8 @@ gmg_status gmg_restrict(gmg_handle h, int l, int fp32, const double* r, double* 
   Level& L = h->L[l];
   Level& C = h->L[l + 1];
   GMG_TRY(to_level(h, l, fp32, r, L.r64, L.r32, s));
-  if (fp32) GMG_TRY(launch_restrict<float>(L, L.r32, C.b32, s));
-  else GMG_TRY(launch_restrict<double>(L, L.r64, C.b64, s));
+  if (fp32) GMG_TRY(launch_restrict<float>(L, L.r32, C.b32, C.x32, s));
+  else GMG_TRY(launch_restrict<double>(L, L.r64, C.b64, C.x64, s));
   return from_level(h, l + 1, fp32, C.b64, C.b32, bc, s);
 }
 
@@ -405,8 +405,8 @@ gmg_status gmg_vcycle(gmg_handle h, int fp32, const double* b, double* x, void* 
   Level& L = h->L[0];
   GMG_TRY(to_level(h, 0, fp32, b, L.b64, L.b32, s));
   GMG_TRY(to_level(h, 0, fp32, x, L.x64, L.x32, s));
-  if (fp32) GMG_TRY(vcycle<float>(h, 0, false, s));
-  else GMG_TRY(vcycle<double>(h, 0, false, s));
+  if (fp32) GMG_TRY(vcycle<float>(h, 0, s));
+  else GMG_TRY(vcycle<double>(h, 0, s));
   return from_level(h, 0, fp32, L.x64, L.x32, x, s);
 }
 

@@ -2,65 +2,156 @@
 //
 // Layout: every level is renumbered colour by colour; the off-diagonal part
 // of A_l is a sliced ELL with 32-row slices stored [k][lane], so the 32 lanes
-// of a warp (one slice) read 32 consecutive values and column indices per k.
-// A Gauss-Seidel colour is one launch over that colour's slices: rows of a
-// colour are never adjacent, so every row reads only other colours' entries
-// of x and the in-place update equals sequential Gauss-Seidel in colour order.
+// of a warp read 32 consecutive values and column indices per k.  A
+// Gauss-Seidel colour is one launch over that colour's slices: rows of a
+// colour are never adjacent, so every row reads only other colours' entries of
+// x and the in-place update equals sequential Gauss-Seidel in colour order.
+// Levels with long rows split each row over G warps (G = 1, 2, 4 or 8; warp
+// `part` takes k = part, part + G, ...), combining the G partial sums in a
+// fixed order, so the dependent-load chain per row is G times shorter.
 // The restriction P_l^T is a sliced ELL over the coarse rows (a gather: no
-// atomics, a fixed summation order).  The prolongation reads three packed
-// (index, weight) slots per fine row.  The coarsest level applies the
+// atomics, a fixed summation order); it also clears the coarse iterate (the
+// recursive call of Alg. 2 starts from zero).  The prolongation reads three
+// packed (index, weight) slots per fine row.  The coarsest level applies the
 // explicit inverse of its FP64 Cholesky factor as a warp-per-row GEMV.
+//
+// Launches use programmatic dependent launch: a kernel may start while its
+// predecessor drains; it loads only setup-time data (matrix values, column
+// indices, inverse diagonal) before `griddepcontrol.wait`, and everything the
+// previous kernel may write after it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <string>
+#include <utility>
 
 #include "gmg_cycle.cuh"
 
 namespace gmg {
 
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------------ kernels
 
-template <class T>
+constexpr int kPrefetch = 8;  // matrix entries per lane loaded before the dependency wait
+
+// Per-lane view of a sliced-ELL row split over G warps.
+struct RowPart {
+  bool active;
+  int nk;        // entries of this row handled by this warp
+  int64_t e;     // first entry
+  int64_t row;
+};
+
+template <int G>
+__device__ __forceinline__ RowPart row_part(int64_t s, int64_t s_end, const int64_t* __restrict__ ptr,
+                                            const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
+                                            int part, int lane) {
+  RowPart p{false, 0, 0, 0};
+  if (s < s_end) {
+    p.active = lane < nrow[s];
+    const int64_t e0 = ptr[s];
+    const int w = (int)((ptr[s + 1] - e0) >> 5);
+    p.nk = (p.active && part < w) ? (w - part + G - 1) / G : 0;
+    p.e = e0 + (int64_t)part * 32 + lane;
+    p.row = row0[s] + lane;
+  }
+  return p;
+}
+
+// sum_k a_rk x_{c_rk} over this warp's share of row r; the first kPrefetch
+// values and columns were loaded before the wait.
+template <class T, int G>
+__device__ __forceinline__ T row_dot(const RowPart& p, const T (&pv)[kPrefetch], const int (&pc)[kPrefetch],
+                                     const int32_t* __restrict__ col, const T* __restrict__ val, const T* x) {
+  T acc = 0;
+#pragma unroll
+  for (int q = 0; q < kPrefetch; ++q)
+    if (q < p.nk) acc += pv[q] * x[pc[q]];
+  for (int q = kPrefetch; q < p.nk; ++q) {
+    const int64_t e = p.e + (int64_t)q * G * 32;
+    acc += val[e] * x[col[e]];
+  }
+  return acc;
+}
+
+template <class T, int G>
+__device__ __forceinline__ void prefetch_row(const RowPart& p, const int32_t* __restrict__ col,
+                                             const T* __restrict__ val, T (&pv)[kPrefetch], int (&pc)[kPrefetch]) {
+#pragma unroll
+  for (int q = 0; q < kPrefetch; ++q) {
+    if (q < p.nk) {
+      const int64_t e = p.e + (int64_t)q * G * 32;
+      pv[q] = val[e];
+      pc[q] = col[e];
+    } else {
+      pv[q] = 0;
+      pc[q] = 0;
+    }
+  }
+}
+
+// Combines the G partial sums of a row in warp order (part 0 first).
+template <class T, int G>
+__device__ __forceinline__ T combine_parts(T acc, int warp, int lane) {
+  if constexpr (G > 1) {
+    __shared__ T red[8][32];
+    red[warp][lane] = acc;
+    __syncthreads();
+    if (warp % G == 0) {
+#pragma unroll
+      for (int g = 1; g < G; ++g) acc += red[warp + g][lane];
+    }
+  }
+  return acc;
+}
+
+// One colour of a Gauss-Seidel sweep: x_r = (b_r - sum_{k != r} a_rk x_k) / a_rr
+// for the rows of slices [s0, s1).
+template <class T, int G>
 __global__ void __launch_bounds__(256) k_gs(int64_t s0, int64_t s1, const int64_t* __restrict__ ptr,
                                             const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
                                             const int32_t* __restrict__ col, const T* __restrict__ val,
-                                            const T* __restrict__ dinv, const T* __restrict__ b, T* x) {
-  const int64_t s = s0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (s >= s1 || lane >= nrow[s]) return;
-  const int64_t r = row0[s] + lane;
-  const int64_t e0 = ptr[s];
-  const int w = (int)((ptr[s + 1] - e0) >> 5);
-  const T* xr = x;  // entries of other colours: not written by this launch
-  T acc = 0;
-  int64_t e = e0 + lane;
-#pragma unroll 4
-  for (int k = 0; k < w; ++k, e += 32) acc += val[e] * __ldg(xr + col[e]);
-  x[r] = (b[r] - acc) * dinv[r];
+                                            const T* __restrict__ dinv, const T* b, T* x) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, part = warp % G;
+  const int64_t s = s0 + (int64_t)blockIdx.x * (8 / G) + warp / G;
+  const RowPart p = row_part<G>(s, s1, ptr, row0, nrow, part, lane);
+  T pv[kPrefetch];
+  int pc[kPrefetch];
+  prefetch_row<T, G>(p, col, val, pv, pc);
+  const T di = (part == 0 && p.active) ? dinv[p.row] : T(0);
+  pdl_wait();
+  pdl_trigger();
+  T acc = row_dot<T, G>(p, pv, pc, col, val, x);
+  acc = combine_parts<T, G>(acc, warp, lane);
+  if (part == 0 && p.active) x[p.row] = (b[p.row] - acc) * di;
 }
 
-template <class T>
+// r = b - A x over all slices; with `partial`, per-block sums of r^2.
+template <class T, int G>
 __global__ void __launch_bounds__(256) k_residual(int64_t nslice, const int64_t* __restrict__ ptr,
                                                   const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
-                                                  const T* __restrict__ diag, const T* __restrict__ x,
-                                                  const T* __restrict__ b, T* __restrict__ r,
+                                                  const T* __restrict__ diag, const T* x, const T* b, T* r,
                                                   double* __restrict__ partial) {
-  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, part = warp % G;
+  const int64_t s = (int64_t)blockIdx.x * (8 / G) + warp / G;
+  const RowPart p = row_part<G>(s, nslice, ptr, row0, nrow, part, lane);
+  T pv[kPrefetch];
+  int pc[kPrefetch];
+  prefetch_row<T, G>(p, col, val, pv, pc);
+  const T d = (part == 0 && p.active) ? diag[p.row] : T(0);
+  pdl_wait();
+  pdl_trigger();
+  T acc = row_dot<T, G>(p, pv, pc, col, val, x);
+  acc = combine_parts<T, G>(acc, warp, lane);
   double sq = 0.0;
-  if (s < nslice && lane < nrow[s]) {
-    const int64_t row = row0[s] + lane;
-    const int64_t e0 = ptr[s];
-    const int w = (int)((ptr[s + 1] - e0) >> 5);
-    T acc = diag[row] * x[row];
-    int64_t e = e0 + lane;
-#pragma unroll 4
-    for (int k = 0; k < w; ++k, e += 32) acc += val[e] * x[col[e]];
-    const T rv = b[row] - acc;
-    r[row] = rv;
+  if (part == 0 && p.active) {
+    const T rv = b[p.row] - (acc + d * x[p.row]);
+    r[p.row] = rv;
     sq = (double)rv * (double)rv;
   }
   if (partial) {  // fixed-shape block reduction of r^2
@@ -79,21 +170,21 @@ __global__ void __launch_bounds__(256) k_residual(int64_t nslice, const int64_t*
 __global__ void __launch_bounds__(256) k_spmv_dot(int64_t nslice, const int64_t* __restrict__ ptr,
                                                   const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
                                                   const int32_t* __restrict__ col, const double* __restrict__ val,
-                                                  const double* __restrict__ diag, const double* __restrict__ p,
-                                                  double* __restrict__ q, double* __restrict__ partial) {
-  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                                                  const double* __restrict__ diag, const double* p,
+                                                  double* q, double* __restrict__ partial) {
   const int lane = threadIdx.x & 31;
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const RowPart rp = row_part<1>(s, nslice, ptr, row0, nrow, 0, lane);
+  double pv[kPrefetch];
+  int pc[kPrefetch];
+  prefetch_row<double, 1>(rp, col, val, pv, pc);
+  pdl_wait();
+  pdl_trigger();
   double pq = 0.0;
-  if (s < nslice && lane < nrow[s]) {
-    const int64_t row = row0[s] + lane;
-    const int64_t e0 = ptr[s];
-    const int w = (int)((ptr[s + 1] - e0) >> 5);
-    double acc = diag[row] * p[row];
-    int64_t e = e0 + lane;
-#pragma unroll 4
-    for (int k = 0; k < w; ++k, e += 32) acc += val[e] * p[col[e]];
-    q[row] = acc;
-    pq = p[row] * acc;
+  if (rp.active) {
+    const double acc = row_dot<double, 1>(rp, pv, pc, col, val, p) + diag[rp.row] * p[rp.row];
+    q[rp.row] = acc;
+    pq = p[rp.row] * acc;
   }
   __shared__ double red[256];
   red[threadIdx.x] = pq;
@@ -105,37 +196,54 @@ __global__ void __launch_bounds__(256) k_spmv_dot(int64_t nslice, const int64_t*
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
+// bc = P^T r (gather over the transpose) and xc = 0 (the coarse iterate of the
+// recursive call starts from zero).
 template <class T>
 __global__ void __launch_bounds__(256) k_restrict(int64_t nslice, const int64_t* __restrict__ ptr,
                                                   const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
                                                   const int32_t* __restrict__ col, const T* __restrict__ w,
-                                                  const T* __restrict__ r, T* __restrict__ bc) {
-  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                                                  const T* r, T* bc, T* xc) {
   const int lane = threadIdx.x & 31;
-  if (s >= nslice || lane >= nrow[s]) return;
-  const int64_t e0 = ptr[s];
-  const int wd = (int)((ptr[s + 1] - e0) >> 5);
-  T acc = 0;
-  int64_t e = e0 + lane;
-  for (int k = 0; k < wd; ++k, e += 32) acc += w[e] * r[col[e]];
-  bc[row0[s] + lane] = acc;
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const RowPart p = row_part<1>(s, nslice, ptr, row0, nrow, 0, lane);
+  T pv[kPrefetch];
+  int pc[kPrefetch];
+  prefetch_row<T, 1>(p, col, w, pv, pc);
+  pdl_wait();
+  pdl_trigger();
+  if (!p.active) return;
+  const T acc = row_dot<T, 1>(p, pv, pc, col, w, r);
+  bc[p.row] = acc;
+  xc[p.row] = T(0);
 }
 
+// x += P u (three packed slots per fine row).
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong(int64_t n, const int32_t* __restrict__ idx, const T* __restrict__ w,
-                                                 const T* __restrict__ u, T* __restrict__ x) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q = 3 * i;
-    x[i] += w[q] * u[idx[q]] + w[q + 1] * u[idx[q + 1]] + w[q + 2] * u[idx[q + 2]];
+                                                 const T* u, T* x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int i0 = 0, i1 = 0, i2 = 0;
+  T w0 = 0, w1 = 0, w2 = 0;
+  if (i < n) {
+    i0 = idx[3 * i];
+    i1 = idx[3 * i + 1];
+    i2 = idx[3 * i + 2];
+    w0 = w[3 * i];
+    w1 = w[3 * i + 1];
+    w2 = w[3 * i + 2];
   }
+  pdl_wait();
+  pdl_trigger();
+  if (i < n) x[i] += w0 * u[i0] + w1 * u[i1] + w2 * u[i2];
 }
 
 // x = Ainv b, one warp per row, FP64 accumulation in both precisions.
 template <class T>
-__global__ void __launch_bounds__(256) k_coarse(int n, const double* __restrict__ Ainv, const T* __restrict__ b,
-                                                T* __restrict__ x) {
+__global__ void __launch_bounds__(256) k_coarse(int n, const double* __restrict__ Ainv, const T* b, T* x) {
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  pdl_wait();
+  pdl_trigger();
   if (row >= n) return;
   const double* a = Ainv + (int64_t)row * n;
   double s = 0.0;
@@ -144,34 +252,51 @@ __global__ void __launch_bounds__(256) k_coarse(int n, const double* __restrict_
   if (lane == 0) x[row] = (T)s;
 }
 
-__global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
-                         double* __restrict__ dst) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = src[perm[i]];
+#define GRID_LOOP(i, n) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const double* src, double* dst) {
+  pdl_wait();
+  pdl_trigger();
+  GRID_LOOP(i, n) dst[i] = src[perm[i]];
 }
-__global__ void k_scatter_vec(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
-                              double* __restrict__ dst) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[perm[i]] = src[i];
+__global__ void k_scatter_vec(int64_t n, const int32_t* __restrict__ perm, const double* src, double* dst) {
+  pdl_wait();
+  pdl_trigger();
+  GRID_LOOP(i, n) dst[perm[i]] = src[i];
 }
-__global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+__global__ void k_d2f(int64_t n, const double* a, float* b) {
+  pdl_wait();
+  pdl_trigger();
+  GRID_LOOP(i, n) b[i] = (float)a[i];
 }
-__global__ void k_f2d(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
+// b32 = (float) r and x32 = 0: the right-hand side and zero initial guess of
+// a correction cycle MGI(0, r).
+__global__ void k_d2f_zero(int64_t n, const double* r, float* b32, float* x32) {
+  pdl_wait();
+  pdl_trigger();
+  GRID_LOOP(i, n) {
+    b32[i] = (float)r[i];
+    x32[i] = 0.f;
+  }
+}
+__global__ void k_f2d(int64_t n, const float* a, double* b) {
+  pdl_wait();
+  pdl_trigger();
+  GRID_LOOP(i, n) b[i] = (double)a[i];
 }
 // x += (double) e
-__global__ void k_add_f2d(int64_t n, const float* __restrict__ e, double* __restrict__ x) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += (double)e[i];
+__global__ void k_add_f2d(int64_t n, const float* e, double* x) {
+  pdl_wait();
+  pdl_trigger();
+  GRID_LOOP(i, n) x[i] += (double)e[i];
 }
 
 // Deterministic dot product: fixed grid, fixed per-thread ranges, fixed tree.
-__global__ void __launch_bounds__(256) k_dot_partial(int64_t n, const double* __restrict__ a,
-                                                     const double* __restrict__ b, double* __restrict__ partial) {
+__global__ void __launch_bounds__(256) k_dot_partial(int64_t n, const double* a, const double* b, double* partial) {
   __shared__ double red[256];
+  pdl_wait();
+  pdl_trigger();
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) s += a[i] * b[i];
   red[threadIdx.x] = s;
@@ -184,8 +309,10 @@ __global__ void __launch_bounds__(256) k_dot_partial(int64_t n, const double* __
 }
 
 // out = sum of `count` partials (one block of 256, fixed order).
-__global__ void k_reduce_final(int count, const double* __restrict__ partial, double* __restrict__ out) {
+__global__ void k_reduce_final(int count, const double* partial, double* out) {
   __shared__ double red[256];
+  pdl_wait();
+  pdl_trigger();
   double s = 0.0;
   for (int i = threadIdx.x; i < count; i += 256) s += partial[i];
   red[threadIdx.x] = s;
@@ -199,100 +326,148 @@ __global__ void k_reduce_final(int count, const double* __restrict__ partial, do
 
 // PCG scalars live on the device: sc[2] = r.z, sc[3] = p.Ap, sc[4] = Polak-
 // Ribiere numerator z.(r - r_old).
-__global__ void k_pcg_axpy(int64_t n, const double* __restrict__ sc, const double* __restrict__ p,
-                           const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r,
-                           double* __restrict__ rold) {
+__global__ void k_pcg_axpy(int64_t n, const double* sc, const double* p, const double* q, double* x, double* r,
+                           double* rold) {
+  pdl_wait();
+  pdl_trigger();
   const double alpha = sc[2] / sc[3];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  GRID_LOOP(i, n) {
     const double ri = r[i];
     rold[i] = ri;
     x[i] += alpha * p[i];
     r[i] = ri - alpha * q[i];
   }
 }
-__global__ void k_pcg_dir(int64_t n, const double* __restrict__ sc, const double* __restrict__ z,
-                          double* __restrict__ p) {
+__global__ void k_pcg_dir(int64_t n, const double* sc, const double* z, double* p) {
+  pdl_wait();
+  pdl_trigger();
   const double beta = sc[4] / sc[2];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+  GRID_LOOP(i, n) p[i] = z[i] + beta * p[i];
 }
-__global__ void k_copy_scalar(const double* __restrict__ src, double* __restrict__ dst) { *dst = *src; }
+__global__ void k_copy_scalar(const double* src, double* dst) {
+  pdl_wait();
+  pdl_trigger();
+  *dst = *src;
+}
 // d = r - rold (for the Polak-Ribiere numerator)
-__global__ void k_sub(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ d) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    d[i] = a[i] - b[i];
+__global__ void k_sub(int64_t n, const double* a, const double* b, double* d) {
+  pdl_wait();
+  pdl_trigger();
+  GRID_LOOP(i, n) d[i] = a[i] - b[i];
+}
+__global__ void k_copy(int64_t n, const double* a, double* b) {
+  pdl_wait();
+  pdl_trigger();
+  GRID_LOOP(i, n) b[i] = a[i];
 }
 
 // ------------------------------------------------------------------ launchers
 
-static inline int blocks_for(int64_t threads, int per = 256, int cap = 152 * 64) {
-  int64_t g = (threads + per - 1) / per;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
+static bool use_pdl() {
+  static const bool on = [] {
+    const char* e = std::getenv("GMG_NO_PDL");
+    return !(e && e[0] == '1');
+  }();
+  return on;
 }
 
-#define LAUNCH_CK() GMG_LAUNCHED()
+// Launches `k` on `s` with programmatic stream serialisation.
+template <typename... P, typename... A>
+static gmg_status launch(void (*k)(P...), int64_t grid, int block, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)std::max<int64_t>(1, grid));
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = use_pdl() ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+  ++g_launches;
+  if (e != cudaSuccess) {
+    set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
+    return GMG_ERR_CUDA;
+  }
+  return GMG_OK;
+}
+
+static inline int64_t blocks_for(int64_t threads, int per = 256, int64_t cap = 152 * 64) {
+  const int64_t g = (threads + per - 1) / per;
+  return std::max<int64_t>(1, std::min<int64_t>(g, cap));
+}
 
 template <class T>
 gmg_status launch_gs_colour(Level& L, int colour, const T* b, T* x, cudaStream_t s) {
   const int64_t s0 = L.color_slice_off[colour], s1 = L.color_slice_off[colour + 1];
   if (s1 <= s0) return GMG_OK;
-  const int64_t threads = (s1 - s0) * 32;
-  k_gs<T><<<(int)((threads + 255) / 256), 256, 0, s>>>(s0, s1, L.A.ptr, L.A.row0, L.A.nrow, L.A.col,
-                                                      Vec<T>::v(L.A), Vec<T>::dinv(L), b, x);
-  LAUNCH_CK();
-  return GMG_OK;
+  const int G = L.lanes;
+  const int64_t grid = (s1 - s0 + (8 / G) - 1) / (8 / G);
+  const Ell& A = L.A;
+  switch (G) {
+    case 1: return launch(k_gs<T, 1>, grid, 256, s, s0, s1, A.ptr, A.row0, A.nrow, A.col, Vec<T>::v(A), Vec<T>::dinv(L), b, x);
+    case 2: return launch(k_gs<T, 2>, grid, 256, s, s0, s1, A.ptr, A.row0, A.nrow, A.col, Vec<T>::v(A), Vec<T>::dinv(L), b, x);
+    case 4: return launch(k_gs<T, 4>, grid, 256, s, s0, s1, A.ptr, A.row0, A.nrow, A.col, Vec<T>::v(A), Vec<T>::dinv(L), b, x);
+    default: return launch(k_gs<T, 8>, grid, 256, s, s0, s1, A.ptr, A.row0, A.nrow, A.col, Vec<T>::v(A), Vec<T>::dinv(L), b, x);
+  }
+}
+
+template <class T>
+static gmg_status launch_residual_p(Level& L, const T* x, const T* b, T* r, double* partial, cudaStream_t s,
+                                    int64_t* nblocks = nullptr) {
+  const int G = L.lanes;
+  const int64_t grid = (L.A.nslice + (8 / G) - 1) / (8 / G);
+  if (nblocks) *nblocks = grid;
+  const Ell& A = L.A;
+  switch (G) {
+    case 1: return launch(k_residual<T, 1>, grid, 256, s, A.nslice, A.ptr, A.row0, A.nrow, A.col, Vec<T>::v(A), Vec<T>::diag(L), x, b, r, partial);
+    case 2: return launch(k_residual<T, 2>, grid, 256, s, A.nslice, A.ptr, A.row0, A.nrow, A.col, Vec<T>::v(A), Vec<T>::diag(L), x, b, r, partial);
+    case 4: return launch(k_residual<T, 4>, grid, 256, s, A.nslice, A.ptr, A.row0, A.nrow, A.col, Vec<T>::v(A), Vec<T>::diag(L), x, b, r, partial);
+    default: return launch(k_residual<T, 8>, grid, 256, s, A.nslice, A.ptr, A.row0, A.nrow, A.col, Vec<T>::v(A), Vec<T>::diag(L), x, b, r, partial);
+  }
 }
 
 template <class T>
 gmg_status launch_residual(Level& L, const T* x, const T* b, T* r, cudaStream_t s) {
-  const int64_t threads = L.A.nslice * 32;
-  k_residual<T><<<(int)((threads + 255) / 256), 256, 0, s>>>(L.A.nslice, L.A.ptr, L.A.row0, L.A.nrow, L.A.col,
-                                                            Vec<T>::v(L.A), Vec<T>::diag(L), x, b, r, nullptr);
-  LAUNCH_CK();
-  return GMG_OK;
+  return launch_residual_p<T>(L, x, b, r, nullptr, s);
 }
 
 template <class T>
-gmg_status launch_restrict(Level& L, const T* r, T* bc, cudaStream_t s) {
-  const int64_t threads = L.R.nslice * 32;
-  k_restrict<T><<<(int)((threads + 255) / 256), 256, 0, s>>>(L.R.nslice, L.R.ptr, L.R.row0, L.R.nrow, L.R.col,
-                                                            Vec<T>::v(L.R), r, bc);
-  LAUNCH_CK();
-  return GMG_OK;
+gmg_status launch_restrict(Level& L, const T* r, T* bc, T* xc, cudaStream_t s) {
+  const Ell& R = L.R;
+  return launch(k_restrict<T>, blocks_for(R.nslice * 32, 256, INT32_MAX), 256, s, R.nslice, R.ptr, R.row0, R.nrow,
+                R.col, Vec<T>::v(R), r, bc, xc);
 }
 
 template <class T>
 gmg_status launch_prolong(Level& L, const T* u, T* x, cudaStream_t s) {
-  k_prolong<T><<<blocks_for(L.n), 256, 0, s>>>(L.n, L.p_idx, Vec<T>::pw(L), u, x);
-  LAUNCH_CK();
-  return GMG_OK;
+  return launch(k_prolong<T>, blocks_for(L.n, 256, INT32_MAX), 256, s, L.n, L.p_idx, Vec<T>::pw(L), u, x);
 }
 
 template <class T>
 gmg_status launch_coarse(gmg_ctx* c, const T* b, T* x, cudaStream_t s) {
   const int n = (int)c->nco;
-  k_coarse<T><<<(n * 32 + 255) / 256, 256, 0, s>>>(n, c->Ainv, b, x);
-  LAUNCH_CK();
-  return GMG_OK;
+  return launch(k_coarse<T>, (n * 32 + 255) / 256, 256, s, n, (const double*)c->Ainv, b, x);
 }
 
-// MGI(x_l, b_l, l) of Alg. 2 on the level's own vectors.
+// MGI(x_l, b_l, l) of Alg. 2 on the level's own vectors.  x_l holds the
+// initial iterate (zero for every l > 0: the restriction clears it).
 template <class T>
-gmg_status vcycle(gmg_ctx* c, int l, bool zero_x, cudaStream_t s) {
+gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s) {
   Level& L = c->L[l];
   T* x = Vec<T>::x(L);
   T* b = Vec<T>::b(L);
   if (l == c->nlev - 1) return launch_coarse<T>(c, b, x, s);
   Level& C = c->L[l + 1];
   const bool prof = c->prof && l == 0;
-  if (zero_x) GMG_CK(cudaMemsetAsync(x, 0, sizeof(T) * (size_t)L.n, s));
   if (prof) GMG_CK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
   for (int it = 0; it < c->opt.nu_pre; ++it)
     for (int k = 0; k < L.ncolor; ++k) GMG_TRY(launch_gs_colour<T>(L, k, b, x, s));
   if (prof) GMG_CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
   GMG_TRY(launch_residual<T>(L, x, b, Vec<T>::r(L), s));
-  GMG_TRY(launch_restrict<T>(L, Vec<T>::r(L), Vec<T>::b(C), s));
-  GMG_TRY(vcycle<T>(c, l + 1, true, s));
+  GMG_TRY(launch_restrict<T>(L, Vec<T>::r(L), Vec<T>::b(C), Vec<T>::x(C), s));
+  GMG_TRY(vcycle<T>(c, l + 1, s));
   GMG_TRY(launch_prolong<T>(L, Vec<T>::x(C), x, s));
   if (prof) GMG_CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
   for (int it = 0; it < c->opt.nu_post; ++it)
@@ -308,76 +483,58 @@ template gmg_status launch_gs_colour<double>(Level&, int, const double*, double*
 template gmg_status launch_gs_colour<float>(Level&, int, const float*, float*, cudaStream_t);
 template gmg_status launch_residual<double>(Level&, const double*, const double*, double*, cudaStream_t);
 template gmg_status launch_residual<float>(Level&, const float*, const float*, float*, cudaStream_t);
-template gmg_status launch_restrict<double>(Level&, const double*, double*, cudaStream_t);
-template gmg_status launch_restrict<float>(Level&, const float*, float*, cudaStream_t);
+template gmg_status launch_restrict<double>(Level&, const double*, double*, double*, cudaStream_t);
+template gmg_status launch_restrict<float>(Level&, const float*, float*, float*, cudaStream_t);
 template gmg_status launch_prolong<double>(Level&, const double*, double*, cudaStream_t);
 template gmg_status launch_prolong<float>(Level&, const float*, float*, cudaStream_t);
 template gmg_status launch_coarse<double>(gmg_ctx*, const double*, double*, cudaStream_t);
 template gmg_status launch_coarse<float>(gmg_ctx*, const float*, float*, cudaStream_t);
-template gmg_status vcycle<double>(gmg_ctx*, int, bool, cudaStream_t);
-template gmg_status vcycle<float>(gmg_ctx*, int, bool, cudaStream_t);
+template gmg_status vcycle<double>(gmg_ctx*, int, cudaStream_t);
+template gmg_status vcycle<float>(gmg_ctx*, int, cudaStream_t);
 
 gmg_status launch_gather(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t s) {
-  k_gather<<<blocks_for(n), 256, 0, s>>>(n, perm, src, dst);
-  LAUNCH_CK();
-  return GMG_OK;
+  return launch(k_gather, blocks_for(n), 256, s, n, perm, src, dst);
 }
 gmg_status launch_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t s) {
-  k_scatter_vec<<<blocks_for(n), 256, 0, s>>>(n, perm, src, dst);
-  LAUNCH_CK();
-  return GMG_OK;
+  return launch(k_scatter_vec, blocks_for(n), 256, s, n, perm, src, dst);
 }
 gmg_status launch_d2f(int64_t n, const double* a, float* b, cudaStream_t s) {
-  k_d2f<<<blocks_for(n), 256, 0, s>>>(n, a, b);
-  LAUNCH_CK();
-  return GMG_OK;
+  return launch(k_d2f, blocks_for(n), 256, s, n, a, b);
 }
 gmg_status launch_f2d(int64_t n, const float* a, double* b, cudaStream_t s) {
-  k_f2d<<<blocks_for(n), 256, 0, s>>>(n, a, b);
-  LAUNCH_CK();
-  return GMG_OK;
+  return launch(k_f2d, blocks_for(n), 256, s, n, a, b);
 }
 
 // ------------------------------------------------------------------ outer iteration
 
-
 // rs = bs - A xs (FP64, finest level) and scal[slot] = ||rs||^2.
 static gmg_status outer_residual(gmg_ctx* c, int slot, cudaStream_t s) {
   Level& L = c->L[0];
-  const int64_t threads = L.A.nslice * 32;
-  const int nb = (int)((threads + 255) / 256);
-  k_residual<double><<<nb, 256, 0, s>>>(L.A.nslice, L.A.ptr, L.A.row0, L.A.nrow, L.A.col, L.A.v64, L.diag64, c->xs,
-                                        c->bs, c->rs, c->red);
-  LAUNCH_CK();
-  k_reduce_final<<<1, 256, 0, s>>>(nb, c->red, c->scal + slot);
-  LAUNCH_CK();
-  return GMG_OK;
+  int64_t nb = 0;
+  GMG_TRY(launch_residual_p<double>(L, c->xs, c->bs, c->rs, c->red, s, &nb));
+  return launch(k_reduce_final, 1, 256, s, (int)nb, (const double*)c->red, c->scal + slot);
 }
 
 static gmg_status dot(gmg_ctx* c, int64_t n, const double* a, const double* b, int slot, cudaStream_t s) {
-  k_dot_partial<<<kRedBlocks, 256, 0, s>>>(n, a, b, c->red);
-  LAUNCH_CK();
-  k_reduce_final<<<1, 256, 0, s>>>(kRedBlocks, c->red, c->scal + slot);
-  LAUNCH_CK();
-  return GMG_OK;
+  GMG_TRY(launch(k_dot_partial, kRedBlocks, 256, s, n, a, b, c->red));
+  return launch(k_reduce_final, 1, 256, s, kRedBlocks, (const double*)c->red, c->scal + slot);
 }
 
 // A finest-level V-cycle, bracketed by timing events when profiling is on.
 template <class T>
-static gmg_status timed_vcycle(gmg_ctx* c, bool zero_x, cudaStream_t s) {
+static gmg_status timed_vcycle(gmg_ctx* c, cudaStream_t s) {
   if (c->prof) GMG_CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
-  GMG_TRY(vcycle<T>(c, 0, zero_x, s));
+  GMG_TRY(vcycle<T>(c, 0, s));
   if (c->prof) GMG_CK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
   return GMG_OK;
 }
 
-// z = V(r) with one FP32 V-cycle (zero initial guess), widened to FP64.
+// z = MGI32(0, r), widened to FP64.
 static gmg_status precond32(gmg_ctx* c, const double* r, double* z, cudaStream_t s) {
   Level& L = c->L[0];
-  GMG_TRY(launch_d2f(L.n, r, L.b32, s));
-  GMG_TRY(timed_vcycle<float>(c, true, s));
-  GMG_TRY(launch_f2d(L.n, L.x32, z, s));
-  return GMG_OK;
+  GMG_TRY(launch(k_d2f_zero, blocks_for(L.n), 256, s, L.n, r, L.b32, L.x32));
+  GMG_TRY(timed_vcycle<float>(c, s));
+  return launch_f2d(L.n, L.x32, z, s);
 }
 
 // One outer iteration (captured as a graph when enabled).
@@ -390,38 +547,30 @@ gmg_status iteration_body(gmg_ctx* c, int mode, int seg, cudaStream_t s) {
   Level& L = c->L[0];
   const int64_t n = L.n;
   if (mode == GMG_FP64) {
-    GMG_TRY(timed_vcycle<double>(c, false, s));  // level-0 x64/b64 alias xs/bs
+    GMG_TRY(timed_vcycle<double>(c, s));  // level-0 x64/b64 alias xs/bs
     return outer_residual(c, S_RR, s);
   }
   if (mode == GMG_FP32_REFINE) {
-    GMG_TRY(launch_d2f(n, c->rs, L.b32, s));
-    GMG_TRY(timed_vcycle<float>(c, true, s));
-    k_add_f2d<<<blocks_for(n), 256, 0, s>>>(n, L.x32, c->xs);
-    LAUNCH_CK();
+    GMG_TRY(launch(k_d2f_zero, blocks_for(n), 256, s, n, (const double*)c->rs, L.b32, L.x32));
+    GMG_TRY(timed_vcycle<float>(c, s));
+    GMG_TRY(launch(k_add_f2d, blocks_for(n), 256, s, n, (const float*)L.x32, c->xs));
     return outer_residual(c, S_RR, s);
   }
   if (seg == 0) {
-    const int64_t threads = L.A.nslice * 32;
-    const int nb = (int)((threads + 255) / 256);
-    k_spmv_dot<<<nb, 256, 0, s>>>(L.A.nslice, L.A.ptr, L.A.row0, L.A.nrow, L.A.col, L.A.v64, L.diag64, c->ps,
-                                  c->qs, c->red);
-    LAUNCH_CK();
-    k_reduce_final<<<1, 256, 0, s>>>(nb, c->red, c->scal + S_PQ);
-    LAUNCH_CK();
-    k_pcg_axpy<<<blocks_for(n), 256, 0, s>>>(n, c->scal, c->ps, c->qs, c->xs, c->rs, c->ros);
-    LAUNCH_CK();
+    const int64_t nb = (L.A.nslice * 32 + 255) / 256;
+    GMG_TRY(launch(k_spmv_dot, nb, 256, s, L.A.nslice, L.A.ptr, L.A.row0, L.A.nrow, L.A.col, L.A.v64, L.diag64,
+                   (const double*)c->ps, c->qs, c->red));
+    GMG_TRY(launch(k_reduce_final, 1, 256, s, (int)nb, (const double*)c->red, c->scal + S_PQ));
+    GMG_TRY(launch(k_pcg_axpy, blocks_for(n), 256, s, n, (const double*)c->scal, (const double*)c->ps,
+                   (const double*)c->qs, c->xs, c->rs, c->ros));
     return dot(c, n, c->rs, c->rs, S_RR, s);
   }
   GMG_TRY(precond32(c, c->rs, c->zs, s));
-  k_sub<<<blocks_for(n), 256, 0, s>>>(n, c->rs, c->ros, c->qs);
-  LAUNCH_CK();
+  GMG_TRY(launch(k_sub, blocks_for(n), 256, s, n, (const double*)c->rs, (const double*)c->ros, c->qs));
   GMG_TRY(dot(c, n, c->zs, c->qs, S_NUM, s));
   GMG_TRY(dot(c, n, c->rs, c->zs, S_RZN, s));
-  k_pcg_dir<<<blocks_for(n), 256, 0, s>>>(n, c->scal, c->zs, c->ps);
-  LAUNCH_CK();
-  k_copy_scalar<<<1, 1, 0, s>>>(c->scal + S_RZN, c->scal + S_RZ);
-  LAUNCH_CK();
-  return GMG_OK;
+  GMG_TRY(launch(k_pcg_dir, blocks_for(n), 256, s, n, (const double*)c->scal, (const double*)c->zs, c->ps));
+  return launch(k_copy_scalar, 1, 1, s, (const double*)(c->scal + S_RZN), c->scal + S_RZ);
 }
 
 // PCG start: z = MGI32(0, r), rz = r.z, p = z (r must be current).
@@ -429,8 +578,7 @@ gmg_status pcg_start(gmg_ctx* c, cudaStream_t s) {
   const int64_t n = c->L[0].n;
   GMG_TRY(precond32(c, c->rs, c->zs, s));
   GMG_TRY(dot(c, n, c->rs, c->zs, S_RZ, s));
-  GMG_CK(cudaMemcpyAsync(c->ps, c->zs, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
-  return GMG_OK;
+  return launch(k_copy, blocks_for(n), 256, s, n, (const double*)c->zs, c->ps);
 }
 
 gmg_status outer_residual_norm(gmg_ctx* c, cudaStream_t s) { return outer_residual(c, S_RR, s); }

@@ -32,10 +32,10 @@ template <> struct Vec<float> {
 // host launchers (gmg_cycle.cu)
 template <class T> gmg_status launch_gs_colour(Level& L, int colour, const T* b, T* x, cudaStream_t s);
 template <class T> gmg_status launch_residual(Level& L, const T* x, const T* b, T* r, cudaStream_t s);
-template <class T> gmg_status launch_restrict(Level& L, const T* r, T* bc, cudaStream_t s);
+template <class T> gmg_status launch_restrict(Level& L, const T* r, T* bc, T* xc, cudaStream_t s);
 template <class T> gmg_status launch_prolong(Level& L, const T* u, T* x, cudaStream_t s);
 template <class T> gmg_status launch_coarse(gmg_ctx* c, const T* b, T* x, cudaStream_t s);
-template <class T> gmg_status vcycle(gmg_ctx* c, int l, bool zero_x, cudaStream_t s);
+template <class T> gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s);
 
 gmg_status launch_d2f(int64_t n, const double* a, float* b, cudaStream_t s);
 gmg_status launch_f2d(int64_t n, const float* a, double* b, cudaStream_t s);

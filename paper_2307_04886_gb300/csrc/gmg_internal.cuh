@@ -86,6 +86,7 @@ struct Ell {
 struct Level {
   int64_t n = 0, nnz = 0;
   int ncolor = 0;
+  int lanes = 1;  // warps sharing one row in Gauss-Seidel / residual (1, 2, 4, 8)
   std::vector<int64_t> color_off;        // host: first permuted row of each colour (+ end)
   std::vector<int64_t> color_slice_off;  // host: first slice of each colour (+ end)
   std::vector<int32_t> h_color;          // host: colour of every row (caller numbering)
@@ -97,6 +98,13 @@ struct Level {
   int32_t* csr_col = nullptr;
   double* csr_val = nullptr;
   int64_t* csr2ell = nullptr;  // ELL slot of each CSR entry, or -1 - row for the diagonal
+  // Galerkin plan of this level (l > 0): terms of entry e are
+  // plan_edge/plan_coef[plan_ptr[e] .. plan_ptr[e+1]) (CSR positions in level
+  // l-1 and P_iJ P_jK), in canonical order; empty below the diagonal
+  int64_t* plan_ptr = nullptr;
+  int32_t* plan_edge = nullptr;
+  double* plan_coef = nullptr;
+  int64_t plan_terms = 0;
   // off-diagonal part of A_l in the permuted numbering
   Ell A;
   double* diag64 = nullptr;
@@ -135,6 +143,7 @@ struct gmg_ctx {
   double* dense = nullptr;  // n x n work / Cholesky factor
   double* Winv = nullptr;   // L^-1
   double* Ainv = nullptr;   // A_lambda^-1 (symmetric, full)
+  double* dbuf = nullptr;   // diagonal factor blocks, then 1 / L_ii
   int* dstatus = nullptr;   // device status words
   // outer iteration (finest level, permuted numbering, FP64)
   double *xs = nullptr, *bs = nullptr, *rs = nullptr, *zs = nullptr, *ps = nullptr, *qs = nullptr, *ros = nullptr;

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -173,53 +174,215 @@ __global__ void k_gal_fill(int64_t nc, const int64_t* __restrict__ pt_rp, const 
   }
 }
 
-// Numeric Galerkin product: for each coarse row J the products
-// P_iJ * A_ij * P_jK are added in the order (i ascending in column J of P,
-// j ascending in row i of A, slot order of row j of P); the lane owning K's
-// hash slot performs every addition into K, so the order is fixed.
-constexpr int kNumWarps = 2;
-__global__ void k_gal_numeric(int64_t nc, const int64_t* __restrict__ pt_rp, const int32_t* __restrict__ pt_col,
-                              const double* __restrict__ pt_w, const int64_t* __restrict__ a_rp,
-                              const int32_t* __restrict__ a_col, const double* __restrict__ a_val,
-                              const int32_t* __restrict__ p_idx, const double* __restrict__ p_w,
-                              const int64_t* __restrict__ c_rp, const int32_t* __restrict__ c_col,
-                              double* __restrict__ c_val) {
-  __shared__ int32_t tab_all[kNumWarps][kHashSlots];
-  __shared__ double acc_all[kNumWarps][kHashSlots];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int32_t* tab = tab_all[warp];
-  double* acc = acc_all[warp];
-  for (int64_t J = (int64_t)blockIdx.x * kNumWarps + warp; J < nc; J += (int64_t)gridDim.x * kNumWarps) {
-    for (int s = lane; s < kHashSlots; s += 32) {
-      tab[s] = -1;
-      acc[s] = 0.0;
+// Galerkin product plan.  For coarse row J the terms (P_iJ P_jK) A_ij of
+// A_{l+1} = P_l^T A_l P_l are enumerated in a canonical order: i ascending in
+// column J of P, j ascending in row i of A, slot order of row j of P.  The
+// symbolic pass records, for every entry (J, K) with K >= J, its terms in
+// that order as (position of A_ij in A_l's CSR, coefficient P_iJ P_jK);
+// entries below the diagonal take the mirrored value.  The numeric pass is
+// then one FP64 gather-dot per entry, summed in plan order.
+constexpr int kPlanWarps = 4;
+constexpr int kPlanChunk = 510;  // terms staged per pass (3 per (i, j) pair)
+constexpr int kSegQ = 256;       // entries of column J of P handled per segment
+struct alignas(16) PlanSmem {
+  double fw[kSegQ];
+  int64_t fk[kSegQ];
+  double pc[kPlanChunk];
+  int32_t pe[kPlanChunk];
+  int32_t tab[kHashSlots];
+  int32_t off[kSegQ + 1];
+  int32_t fill[kMaxRowEntries];
+  int32_t cnt[32];
+  int16_t tpos[kHashSlots];
+  int16_t ps[kPlanChunk];
+  int16_t list[kPlanChunk];
+};
+
+// Loads row J's sorted columns into the hash table (slot -> position).
+__device__ void plan_row_table(PlanSmem& S, int64_t r0, int64_t r1, const int32_t* __restrict__ c_col) {
+  const int lane = threadIdx.x & 31;
+  for (int s = lane; s < kHashSlots; s += 32) S.tab[s] = -1;
+  __syncwarp();
+  for (int64_t a = r0 + lane; a < r1; a += 32) {
+    const int32_t K = c_col[a];
+    hash_insert(S.tab, K);
+  }
+  __syncwarp();
+  for (int64_t a = r0 + lane; a < r1; a += 32) S.tpos[hash_find(S.tab, c_col[a])] = (int16_t)(a - r0);
+  __syncwarp();
+}
+
+// Fine rows, weights, row starts and pair offsets of one segment of column J
+// of P; returns the number of (i, j) pairs.
+__device__ int plan_segment(PlanSmem& S, int64_t seg, int nq, const int32_t* __restrict__ pt_col,
+                            const double* __restrict__ pt_w, const int64_t* __restrict__ a_rp) {
+  const int lane = threadIdx.x & 31;
+  int carry = 0;
+  for (int q0 = 0; q0 < nq; q0 += 32) {
+    const int q = q0 + lane;
+    int len = 0;
+    if (q < nq) {
+      const int32_t i = pt_col[seg + q];
+      S.fw[q] = pt_w[seg + q];
+      S.fk[q] = a_rp[i];
+      len = (int)(a_rp[i + 1] - a_rp[i]);
     }
-    __syncwarp();
-    const int64_t r0 = c_rp[J], r1 = c_rp[J + 1];
-    for (int64_t a = r0 + lane; a < r1; a += 32) hash_insert(tab, c_col[a]);
-    __syncwarp();
-    for (int64_t q = pt_rp[J]; q < pt_rp[J + 1]; ++q) {
-      const int32_t i = pt_col[q];
-      const double wiJ = pt_w[q];
-      for (int64_t k = a_rp[i]; k < a_rp[i + 1]; ++k) {
-        const int64_t j = a_col[k];
-        const double wa = wiJ * a_val[k];
+    int incl = len;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (q < nq) S.off[q + 1] = carry + incl;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) S.off[0] = 0;
+  __syncwarp();
+  return carry;
+}
+
+// Terms of pairs [t0, t0 + np) of the segment: position of (J, K) in row J
+// (-1 when P_jK = 0 or K < J), CSR position of A_ij and P_iJ P_jK.
+__device__ void plan_stage(PlanSmem& S, int64_t J, int nq, int t0, int np, const int32_t* __restrict__ a_col,
+                           const int32_t* __restrict__ p_idx, const double* __restrict__ p_w) {
+  const int lane = threadIdx.x & 31;
+  for (int tt = lane; tt < np; tt += 32) {
+    const int t = t0 + tt;
+    int lo = 0, hi = nq - 1;  // last q with off[q] <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (S.off[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const int64_t k = S.fk[lo] + (t - S.off[lo]);
+    const int64_t j = a_col[k];
+    const double wi = S.fw[lo];
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          const double w = p_w[3 * j + m];
-          if (w != 0.0) {
-            const int s = hash_find(tab, p_idx[3 * j + m]);
-            if (s >= 0 && (s & 31) == lane) acc[s] += wa * w;
-          }
-        }
+    for (int m = 0; m < 3; ++m) {
+      const double w = p_w[3 * j + m];
+      const int32_t K = p_idx[3 * j + m];
+      int pos = -1;
+      if (w != 0.0 && K >= J) pos = S.tpos[hash_find(S.tab, K)];
+      S.ps[3 * tt + m] = (int16_t)pos;
+      S.pe[3 * tt + m] = (int32_t)k;
+      S.pc[3 * tt + m] = __dmul_rn(wi, w);
+    }
+  }
+  __syncwarp();
+}
+
+// Symbolic pass 1: number of terms of every entry (J, K), K >= J.
+__global__ void __launch_bounds__(kPlanWarps * 32)
+    k_gal_plan_count(int64_t nc, const int64_t* __restrict__ pt_rp, const int32_t* __restrict__ pt_col,
+                     const double* __restrict__ pt_w, const int64_t* __restrict__ a_rp,
+                     const int32_t* __restrict__ a_col, const int32_t* __restrict__ p_idx,
+                     const double* __restrict__ p_w, const int64_t* __restrict__ c_rp,
+                     const int32_t* __restrict__ c_col, int64_t* __restrict__ terms) {
+  extern __shared__ unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  PlanSmem& S = reinterpret_cast<PlanSmem*>(smem_raw)[warp];
+  for (int64_t J = (int64_t)blockIdx.x * kPlanWarps + warp; J < nc; J += (int64_t)gridDim.x * kPlanWarps) {
+    const int64_t r0 = c_rp[J], r1 = c_rp[J + 1];
+    const int len = (int)(r1 - r0);
+    plan_row_table(S, r0, r1, c_col);
+    for (int a = lane; a < len; a += 32) S.fill[a] = 0;
+    __syncwarp();
+    for (int64_t seg = pt_rp[J]; seg < pt_rp[J + 1]; seg += kSegQ) {
+      const int64_t left = pt_rp[J + 1] - seg;
+      const int nq = left < kSegQ ? (int)left : kSegQ;
+      const int pairs = plan_segment(S, seg, nq, pt_col, pt_w, a_rp);
+      for (int t0 = 0; t0 < pairs; t0 += kPlanChunk / 3) {
+        const int np = min(kPlanChunk / 3, pairs - t0);
+        plan_stage(S, J, nq, t0, np, a_col, p_idx, p_w);
+        for (int p = lane; p < 3 * np; p += 32)
+          if (S.ps[p] >= 0) atomicAdd(&S.fill[S.ps[p]], 1);
+        __syncwarp();
       }
     }
+    for (int a = lane; a < len; a += 32) terms[r0 + a] = S.fill[a];
     __syncwarp();
-    for (int64_t a = r0 + lane; a < r1; a += 32) {
-      const int s = hash_find(tab, c_col[a]);
-      c_val[a] = s >= 0 ? acc[s] : 0.0;
+  }
+}
+
+// Symbolic pass 2: writes every entry's terms in canonical order.  The lane
+// owning a position (pos & 31) appends that position's terms; products of a
+// chunk are grouped by owner first so all lanes append in parallel.
+__global__ void __launch_bounds__(kPlanWarps * 32)
+    k_gal_plan_fill(int64_t nc, const int64_t* __restrict__ pt_rp, const int32_t* __restrict__ pt_col,
+                    const double* __restrict__ pt_w, const int64_t* __restrict__ a_rp,
+                    const int32_t* __restrict__ a_col, const int32_t* __restrict__ p_idx,
+                    const double* __restrict__ p_w, const int64_t* __restrict__ c_rp,
+                    const int32_t* __restrict__ c_col, const int64_t* __restrict__ plan_ptr,
+                    int32_t* __restrict__ plan_edge, double* __restrict__ plan_coef) {
+  extern __shared__ unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  PlanSmem& S = reinterpret_cast<PlanSmem*>(smem_raw)[warp];
+  for (int64_t J = (int64_t)blockIdx.x * kPlanWarps + warp; J < nc; J += (int64_t)gridDim.x * kPlanWarps) {
+    const int64_t r0 = c_rp[J], r1 = c_rp[J + 1];
+    const int len = (int)(r1 - r0);
+    plan_row_table(S, r0, r1, c_col);
+    for (int a = lane; a < len; a += 32) S.fill[a] = 0;
+    __syncwarp();
+    for (int64_t seg = pt_rp[J]; seg < pt_rp[J + 1]; seg += kSegQ) {
+      const int64_t left = pt_rp[J + 1] - seg;
+      const int nq = left < kSegQ ? (int)left : kSegQ;
+      const int pairs = plan_segment(S, seg, nq, pt_col, pt_w, a_rp);
+      for (int t0 = 0; t0 < pairs; t0 += kPlanChunk / 3) {
+        const int np = min(kPlanChunk / 3, pairs - t0);
+        plan_stage(S, J, nq, t0, np, a_col, p_idx, p_w);
+        const int nprod = 3 * np;
+        S.cnt[lane] = 0;
+        __syncwarp();
+        for (int g0 = 0; g0 < nprod; g0 += 32) {
+          const int p = g0 + lane;
+          const int ps = p < nprod ? S.ps[p] : -1;
+          const int own = ps >= 0 ? (ps & 31) : 32;
+          const unsigned peers = __match_any_sync(0xffffffffu, own);
+          if (own < 32 && lane == __ffs(peers) - 1) S.cnt[own] += __popc(peers);
+          __syncwarp();
+        }
+        const int mine = S.cnt[lane];
+        int start = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, start, o);
+          if (lane >= o) start += v;
+        }
+        start -= mine;
+        __syncwarp();
+        S.cnt[lane] = start;
+        __syncwarp();
+        for (int g0 = 0; g0 < nprod; g0 += 32) {
+          const int p = g0 + lane;
+          const int ps = p < nprod ? S.ps[p] : -1;
+          const int own = ps >= 0 ? (ps & 31) : 32;
+          const unsigned peers = __match_any_sync(0xffffffffu, own);
+          if (own < 32) S.list[S.cnt[own] + __popc(peers & ((1u << lane) - 1u))] = (int16_t)p;
+          __syncwarp();
+          if (own < 32 && lane == __ffs(peers) - 1) S.cnt[own] += __popc(peers);
+          __syncwarp();
+        }
+        for (int q = start; q < start + mine; ++q) {
+          const int p = S.list[q];
+          const int pos = S.ps[p];
+          const int64_t dst = plan_ptr[r0 + pos] + S.fill[pos]++;
+          plan_edge[dst] = S.pe[p];
+          plan_coef[dst] = S.pc[p];
+        }
+        __syncwarp();
+      }
     }
-    __syncwarp();
+  }
+}
+
+// Numeric pass: value of every entry = sum over its plan of coef * A_l value,
+// multiplied and added with separate roundings in plan order.
+__global__ void __launch_bounds__(256)
+    k_gal_apply(int64_t nnz, const int64_t* __restrict__ plan_ptr, const int32_t* __restrict__ plan_edge,
+                const double* __restrict__ plan_coef, const double* __restrict__ a_val, double* __restrict__ c_val) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t t = plan_ptr[e]; t < plan_ptr[e + 1]; ++t)
+      acc = __dadd_rn(acc, __dmul_rn(plan_coef[t], a_val[plan_edge[t]]));
+    c_val[e] = acc;
   }
 }
 
@@ -281,12 +444,39 @@ __global__ void k_csr_to_dense(int64_t n, const int64_t* __restrict__ rp, const 
 }
 
 // ---- dense FP64 Cholesky, right-looking, 32 x 32 blocks ----
-// k_chol_diag (one CTA) factors the diagonal block p in shared memory and
-// writes L_pp back; k_chol_panel then solves the rows below it,
-// L_ip = A_ip L_pp^-T; k_chol_update applies the trailing update.
-// status bit 0: a pivot <= 0.
-__global__ void k_chol_diag(int n, int p, double* __restrict__ A, int* __restrict__ status) {
+// k_chol_panel factors the diagonal block p in every CTA's shared memory
+// (identical arithmetic in every CTA), CTA 0 stores the factor L_pp in Dbuf,
+// and every CTA solves its rows below the block: L_ip = A_ip L_pp^-T.
+// k_chol_update then applies the trailing update; k_chol_store_diag writes
+// the stored diagonal factors into A once all steps are done (block p of A is
+// not read again after step p).  status bit 0: a pivot <= 0.
+__device__ void chol_factor_block(double (&D)[32][33], double (&rdiag)[32], int nb, int* bad) {
+  for (int k = 0; k < nb; ++k) {
+    if (threadIdx.x == 0) {
+      double d = D[k][k];
+      if (!(d > 0.0)) {
+        *bad = 1;
+        d = 1.0;
+      }
+      const double l = sqrt(d);
+      D[k][k] = l;
+      rdiag[k] = 1.0 / l;
+    }
+    __syncthreads();
+    for (int r = k + 1 + threadIdx.x; r < nb; r += blockDim.x) D[r][k] *= rdiag[k];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+      const int r = idx >> 5, c = idx & 31;
+      if (c > k && r >= c && r < nb) D[r][c] -= D[r][k] * D[c][k];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_chol_panel(int n, int p, double* __restrict__ A, double* __restrict__ Dbuf,
+                             int* __restrict__ status) {
   __shared__ double D[32][33];
+  __shared__ double rdiag[32];
   __shared__ int bad;
   const int j0 = p * 32;
   const int nb = min(32, n - j0);
@@ -296,40 +486,14 @@ __global__ void k_chol_diag(int n, int p, double* __restrict__ A, int* __restric
     D[r][c] = (r < nb && c < nb) ? A[(int64_t)(j0 + r) * n + j0 + c] : (r == c ? 1.0 : 0.0);
   }
   __syncthreads();
-  for (int k = 0; k < nb; ++k) {
-    if (threadIdx.x == 0) {
-      double d = D[k][k];
-      if (!(d > 0.0)) {
-        bad = 1;
-        d = 1.0;
-      }
-      D[k][k] = sqrt(d);
-    }
-    __syncthreads();
-    for (int r = k + 1 + threadIdx.x; r < nb; r += blockDim.x) D[r][k] /= D[k][k];
-    __syncthreads();
+  chol_factor_block(D, rdiag, nb, &bad);
+  if (blockIdx.x == 0) {
+    if (bad && threadIdx.x == 0) atomicOr(status, 1);
     for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
       const int r = idx >> 5, c = idx & 31;
-      if (c > k && r >= c && r < nb) D[r][c] -= D[r][k] * D[c][k];
+      Dbuf[(int64_t)p * 1024 + idx] = (c <= r) ? D[r][c] : 0.0;
     }
-    __syncthreads();
   }
-  if (bad && threadIdx.x == 0) atomicOr(status, 1);
-  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-    const int r = idx >> 5, c = idx & 31;
-    if (r < nb && c < nb) A[(int64_t)(j0 + r) * n + j0 + c] = (c <= r) ? D[r][c] : 0.0;
-  }
-}
-
-__global__ void k_chol_panel(int n, int p, double* __restrict__ A) {
-  __shared__ double D[32][33];
-  const int j0 = p * 32;
-  const int nb = min(32, n - j0);
-  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-    const int r = idx >> 5, c = idx & 31;
-    D[r][c] = (r < nb && c < nb) ? A[(int64_t)(j0 + r) * n + j0 + c] : (r == c ? 1.0 : 0.0);
-  }
-  __syncthreads();
   const int i = j0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     double v[32];
@@ -341,12 +505,22 @@ __global__ void k_chol_panel(int n, int p, double* __restrict__ A) {
         double s = v[c];
 #pragma unroll
         for (int k = 0; k < c; ++k) s -= v[k] * D[c][k];
-        v[c] = s / D[c][c];
+        v[c] = s * rdiag[c];
       }
     }
 #pragma unroll
     for (int c = 0; c < 32; ++c)
       if (c < nb) A[(int64_t)i * n + j0 + c] = v[c];
+  }
+}
+
+__global__ void k_chol_store_diag(int n, const double* __restrict__ Dbuf, double* __restrict__ A) {
+  const int p = blockIdx.x;
+  const int j0 = p * 32;
+  const int nb = min(32, n - j0);
+  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+    const int r = idx >> 5, c = idx & 31;
+    if (r < nb && c < nb) A[(int64_t)(j0 + r) * n + j0 + c] = Dbuf[(int64_t)p * 1024 + idx];
   }
 }
 
@@ -387,21 +561,28 @@ __global__ void k_chol_update(int n, int p, double* __restrict__ A) {
   }
 }
 
+// rdiag[i] = 1 / L_ii
+__global__ void k_recip_diag(int n, const double* __restrict__ Lf, double* __restrict__ rdiag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    rdiag[i] = 1.0 / Lf[(int64_t)i * n + i];
+}
+
 // Wt = (L^-1)^T: row k of Wt is column k of L^-1, by forward substitution
 // (one warp per column; Wt must be zero-initialised).
-__global__ void k_tri_inverse(int n, const double* __restrict__ Lf, double* __restrict__ Wt) {
+__global__ void k_tri_inverse(int n, const double* __restrict__ Lf, const double* __restrict__ rdiag,
+                              double* __restrict__ Wt) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
   const int k = warp;
   double* w = Wt + (int64_t)k * n;
-  if (lane == 0) w[k] = 1.0 / Lf[(int64_t)k * n + k];
+  if (lane == 0) w[k] = rdiag[k];
   __syncwarp();
   for (int i = k + 1; i < n; ++i) {
     const double* Li = Lf + (int64_t)i * n;
     double s = 0.0;
     for (int m = k + lane; m < i; m += 32) s += Li[m] * w[m];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) w[i] = -s / Li[i];
+    if (lane == 0) w[i] = -s * rdiag[i];
     __syncwarp();
   }
 }
@@ -569,6 +750,15 @@ static gmg_status build_level_structure(gmg_ctx* c, int l, const int64_t* rp, co
   }
   Arena& a = c->arena;
   GMG_TRY(upload_ell(a, L.A, P, ecol));
+  // Rows longer than a few entries are split over several warps so that the
+  // chain of dependent loads per row stays short (coarse levels carry 15-40
+  // entries per row; the finest mesh level about 6).
+  {
+    const double wavg = P.row0.empty() ? 0.0 : (double)P.ptr.back() / (32.0 * (double)P.row0.size());
+    L.lanes = wavg <= 8.0 ? 1 : wavg <= 16.0 ? 2 : wavg <= 32.0 ? 4 : 8;
+    if (const char* e = std::getenv("GMG_LANES")) L.lanes = std::atoi(e);
+    if (L.lanes != 1 && L.lanes != 2 && L.lanes != 4 && L.lanes != 8) L.lanes = 1;
+  }
   GMG_TRY(upload(a, &L.csr2ell, c2e.data(), c2e.size()));
   GMG_TRY(upload(a, &L.perm, perm.data(), perm.size()));
   GMG_TRY(upload(a, &L.iperm, iperm.data(), iperm.size()));
@@ -688,6 +878,10 @@ static gmg_status galerkin_symbolic(gmg_ctx* c, int l, cudaStream_t s, std::vect
   GMG_CK(cudaMemcpyAsync(hrp.data(), C.csr_rowptr, (nc + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   GMG_CK(cudaStreamSynchronize(s));
   C.nnz = hrp[nc];
+  if (C.nnz >= INT32_MAX || F.nnz >= INT32_MAX) {
+    set_error("Galerkin level " + std::to_string(l + 1) + ": more than 2^31 stored entries");
+    return GMG_ERR_TOO_LARGE;
+  }
   GMG_TRY(c->arena.alloc(&C.csr_col, C.nnz));
   GMG_TRY(c->arena.alloc(&C.csr_val, C.nnz));
   const int g2 = grid_for(nc, kFillWarps, 152 * 32);
@@ -696,6 +890,30 @@ static gmg_status galerkin_symbolic(gmg_ctx* c, int l, cudaStream_t s, std::vect
   GMG_LAUNCHED();
   hcol.resize(C.nnz);
   GMG_CK(cudaMemcpyAsync(hcol.data(), C.csr_col, C.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GMG_CK(cudaStreamSynchronize(s));
+  // product plan of the numeric pass
+  const size_t psm = sizeof(PlanSmem) * kPlanWarps;
+  GMG_CK(cudaFuncSetAttribute(k_gal_plan_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+  GMG_CK(cudaFuncSetAttribute(k_gal_plan_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+  int64_t* terms;
+  GMG_TRY(c->arena.alloc(&terms, (size_t)C.nnz));
+  const int gp = grid_for(nc, kPlanWarps, 152 * 16);
+  k_gal_plan_count<<<gp, kPlanWarps * 32, psm, s>>>(nc, F.pt_rowptr_o, F.pt_col_o, F.pt_w_o, F.csr_rowptr, F.csr_col,
+                                                    F.p_idx_o, F.p_w_o, C.csr_rowptr, C.csr_col, terms);
+  GMG_LAUNCHED();
+  GMG_TRY(c->arena.alloc(&C.plan_ptr, (size_t)C.nnz + 1));
+  k_scan_counts<<<1, 1024, 0, s>>>(C.nnz, terms, C.plan_ptr);
+  GMG_LAUNCHED();
+  int64_t total = 0;
+  GMG_CK(cudaMemcpyAsync(&total, C.plan_ptr + C.nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GMG_CK(cudaStreamSynchronize(s));
+  C.plan_terms = total;
+  GMG_TRY(c->arena.alloc(&C.plan_edge, (size_t)total));
+  GMG_TRY(c->arena.alloc(&C.plan_coef, (size_t)total));
+  k_gal_plan_fill<<<gp, kPlanWarps * 32, psm, s>>>(nc, F.pt_rowptr_o, F.pt_col_o, F.pt_w_o, F.csr_rowptr, F.csr_col,
+                                                   F.p_idx_o, F.p_w_o, C.csr_rowptr, C.csr_col, C.plan_ptr,
+                                                   C.plan_edge, C.plan_coef);
+  GMG_LAUNCHED();
   GMG_CK(cudaStreamSynchronize(s));
   return GMG_OK;
 }
@@ -708,10 +926,8 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s) {
     Level& F = c->L[l];
     if (l > 0) {
       Level& P = c->L[l - 1];
-      const int g = grid_for(F.n, kNumWarps, 152 * 64);
-      k_gal_numeric<<<g, kNumWarps * 32, 0, s>>>(F.n, P.pt_rowptr_o, P.pt_col_o, P.pt_w_o, P.csr_rowptr,
-                                                P.csr_col, P.csr_val, P.p_idx_o, P.p_w_o, F.csr_rowptr, F.csr_col,
-                                                F.csr_val);
+      k_gal_apply<<<grid_for(F.nnz, 256), 256, 0, s>>>(F.nnz, F.plan_ptr, F.plan_edge, F.plan_coef, P.csr_val,
+                                                      F.csr_val);
       GMG_LAUNCHED();
       k_gal_mirror<<<grid_for(F.n, 256), 256, 0, s>>>(F.n, F.csr_rowptr, F.csr_col, F.csr_val);
       GMG_LAUNCHED();
@@ -729,20 +945,20 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s) {
   const int nbk = (n + 31) / 32;
   for (int p = 0; p < nbk; ++p) {
     const int below = n - std::min(n, (p + 1) * 32);
-    k_chol_diag<<<1, 256, 0, s>>>(n, p, c->dense, c->dstatus + 1);
+    k_chol_panel<<<std::max(1, (below + 127) / 128), 128, 0, s>>>(n, p, c->dense, c->dbuf, c->dstatus + 1);
     GMG_LAUNCHED();
-    if (below > 0) {
-      k_chol_panel<<<(below + 127) / 128, 128, 0, s>>>(n, p, c->dense);
-      GMG_LAUNCHED();
-    }
     const int T = nbk - p - 1;
     if (T > 0) {
       k_chol_update<<<T * (T + 1) / 2, 256, 0, s>>>(n, p, c->dense);
       GMG_LAUNCHED();
     }
   }
+  k_chol_store_diag<<<nbk, 256, 0, s>>>(n, c->dbuf, c->dense);
+  GMG_LAUNCHED();
+  k_recip_diag<<<(n + 255) / 256, 256, 0, s>>>(n, c->dense, c->dbuf);
+  GMG_LAUNCHED();
   GMG_CK(cudaMemsetAsync(c->Winv, 0, sizeof(double) * (size_t)n * n, s));
-  k_tri_inverse<<<(n + 3) / 4, 128, 0, s>>>(n, c->dense, c->Winv);
+  k_tri_inverse<<<(n + 3) / 4, 128, 0, s>>>(n, c->dense, c->dbuf, c->Winv);
   GMG_LAUNCHED();
   k_inv_gram<<<nbk * (nbk + 1) / 2, 256, 0, s>>>(n, c->Winv, c->Ainv);
   GMG_LAUNCHED();
@@ -923,6 +1139,7 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   GMG_TRY(a.alloc(&c->dense, (size_t)(c->nco * c->nco)));
   GMG_TRY(a.alloc(&c->Winv, (size_t)(c->nco * c->nco)));
   GMG_TRY(a.alloc(&c->Ainv, (size_t)(c->nco * c->nco)));
+  GMG_TRY(a.alloc(&c->dbuf, (size_t)(((c->nco + 31) / 32) * 1024 + c->nco)));
   // outer-iteration vectors
   const int64_t n = L0.n;
   c->xs = L0.x64;  // the FP64 cycle runs directly on the outer iterate
