@@ -361,6 +361,172 @@ __global__ void k_copy(int64_t n, const double* a, double* b) {
   GRID_LOOP(i, n) b[i] = a[i];
 }
 
+// ------------------------------------------------------------------ small levels
+// The levels at and below `l0` (all small) run as one persistent kernel per
+// V-cycle on a single thread-block cluster: every colour phase, residual,
+// restriction, coarse solve and prolongation of those levels is separated
+// by a hardware cluster barrier instead of a kernel boundary.  Vectors are
+// read through L2 (ld.global.cg): they are written by other CTAs of the
+// cluster between barriers.  Matrix data is setup-time data.
+
+template <class T> struct DV;
+template <> struct DV<float> {
+  __device__ static const float* av(const DevLevel& L) { return L.a_v32; }
+  __device__ static const float* dinv(const DevLevel& L) { return L.dinv32; }
+  __device__ static const float* diag(const DevLevel& L) { return L.diag32; }
+  __device__ static const float* rv(const DevLevel& L) { return L.r_v32; }
+  __device__ static const float* pw(const DevLevel& L) { return L.p_w32; }
+  __device__ static float* x(const DevLevel& L) { return L.x32; }
+  __device__ static float* b(const DevLevel& L) { return L.b32; }
+  __device__ static float* r(const DevLevel& L) { return L.r32; }
+};
+template <> struct DV<double> {
+  __device__ static const double* av(const DevLevel& L) { return L.a_v64; }
+  __device__ static const double* dinv(const DevLevel& L) { return L.dinv64; }
+  __device__ static const double* diag(const DevLevel& L) { return L.diag64; }
+  __device__ static const double* rv(const DevLevel& L) { return L.r_v64; }
+  __device__ static const double* pw(const DevLevel& L) { return L.p_w64; }
+  __device__ static double* x(const DevLevel& L) { return L.x64; }
+  __device__ static double* b(const DevLevel& L) { return L.b64; }
+  __device__ static double* r(const DevLevel& L) { return L.r64; }
+};
+
+__device__ __forceinline__ void cluster_sync() {
+  __syncwarp();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// One Gauss-Seidel colour (mode 0) or the residual over all slices (mode 1)
+// of level L, split over the cluster: G warps of one CTA share a slice.
+template <class T, int G>
+__device__ void cl_rows(const DevLevel& L, int64_t s0, int64_t s1, int mode, int cta, T (&red)[32][33]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, part = warp % G;
+  constexpr int SPC = 32 / G;                 // slices per CTA per round
+  constexpr int SPR = SPC * kClusterCTAs;     // slices per round
+  const int64_t rounds = (s1 - s0 + SPR - 1) / SPR;
+  const T* val = DV<T>::av(L);
+  T* x = DV<T>::x(L);
+  const T* b = DV<T>::b(L);
+  for (int64_t rd = 0; rd < rounds; ++rd) {
+    const int64_t s = s0 + rd * SPR + (int64_t)cta * SPC + warp / G;
+    const RowPart p = row_part<G>(s, s1, L.a_ptr, L.a_row0, L.a_nrow, part, lane);
+    // all matrix loads first, then all gathers: two dependent round trips per row
+    T pv[kPrefetch];
+    int pc[kPrefetch];
+    prefetch_row<T, G>(p, L.a_col, val, pv, pc);
+    T xv[kPrefetch];
+#pragma unroll
+    for (int q = 0; q < kPrefetch; ++q) xv[q] = q < p.nk ? __ldcg(x + pc[q]) : T(0);
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < kPrefetch; ++q) acc += pv[q] * xv[q];
+    for (int q = kPrefetch; q < p.nk; ++q) {
+      const int64_t e = p.e + (int64_t)q * G * 32;
+      acc += val[e] * __ldcg(x + L.a_col[e]);
+    }
+    if constexpr (G > 1) {
+      red[warp][lane] = acc;
+      __syncthreads();
+      if (part == 0) {
+#pragma unroll
+        for (int g = 1; g < G; ++g) acc += red[warp + g][lane];
+      }
+    }
+    if (part == 0 && p.active) {
+      if (mode == 0) {
+        x[p.row] = (__ldcg(b + p.row) - acc) * DV<T>::dinv(L)[p.row];
+      } else {
+        DV<T>::r(L)[p.row] = __ldcg(b + p.row) - (acc + DV<T>::diag(L)[p.row] * __ldcg(x + p.row));
+      }
+    }
+    if constexpr (G > 1) __syncthreads();
+  }
+}
+
+template <class T>
+__device__ void cl_rows_any(const DevLevel& L, int64_t s0, int64_t s1, int mode, int cta, T (&red)[32][33]) {
+  switch (L.lanes) {
+    case 1: cl_rows<T, 1>(L, s0, s1, mode, cta, red); break;
+    case 2: cl_rows<T, 2>(L, s0, s1, mode, cta, red); break;
+    case 4: cl_rows<T, 4>(L, s0, s1, mode, cta, red); break;
+    default: cl_rows<T, 8>(L, s0, s1, mode, cta, red); break;
+  }
+}
+
+// half 0: pre-smoothing, residual and restriction of levels l0 .. lambda-1
+// (down to the coarsest right-hand side); half 1: prolongation and
+// post-smoothing from lambda-1 back up to l0.  The coarsest solve between
+// the halves runs on the whole GPU (its FP64 GEMV needs every SM's FP64 pipe).
+template <class T>
+__global__ void __launch_bounds__(1024) k_cluster_cycle(const DevLevel* __restrict__ lv, int l0, int nlev, int half,
+                                                        int nu_pre, int nu_post, int post_forward) {
+  __shared__ T red[32][33];
+  const int cta = (int)cluster_rank();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gwarp = cta * 32 + warp;                         // warp index in the cluster
+  const int64_t gthread = (int64_t)cta * 1024 + threadIdx.x;  // thread index in the cluster
+  constexpr int kWarps = 32 * kClusterCTAs;
+  constexpr int kThreads = 1024 * kClusterCTAs;
+  pdl_wait();
+  pdl_trigger();
+  if (half == 0) {
+    for (int l = l0; l < nlev - 1; ++l) {
+      const DevLevel& L = lv[l];
+      for (int it = 0; it < nu_pre; ++it)
+        for (int k = 0; k < L.ncolor; ++k) {
+          cl_rows_any<T>(L, L.cso[k], L.cso[k + 1], 0, cta, red);
+          cluster_sync();
+        }
+      cl_rows_any<T>(L, 0, L.nslice, 1, cta, red);
+      cluster_sync();
+      // restriction into level l+1 (clears its iterate)
+      const DevLevel& C = lv[l + 1];
+      const T* r = DV<T>::r(L);
+      const T* rw = DV<T>::rv(L);
+      for (int64_t s = gwarp; s < L.r_nslice; s += kWarps) {
+        if (lane >= L.r_nrow[s]) continue;
+        const int64_t e0 = L.r_ptr[s] + lane;
+        const int wd = (int)((L.r_ptr[s + 1] - L.r_ptr[s]) >> 5);
+        T acc = 0;
+#pragma unroll 8
+        for (int k = 0; k < wd; ++k) {
+          const int64_t e = e0 + (int64_t)k * 32;
+          acc += rw[e] * __ldcg(r + L.r_col[e]);
+        }
+        const int64_t row = L.r_row0[s] + lane;
+        DV<T>::b(C)[row] = acc;
+        DV<T>::x(C)[row] = T(0);
+      }
+      if (l + 1 < nlev - 1) cluster_sync();
+    }
+    return;
+  }
+  for (int l = nlev - 2; l >= l0; --l) {
+    const DevLevel& L = lv[l];
+    const DevLevel& C = lv[l + 1];
+    T* x = DV<T>::x(L);
+    const T* u = DV<T>::x(C);
+    const T* w = DV<T>::pw(L);
+    for (int64_t i = gthread; i < L.n; i += kThreads) {
+      const int64_t q = 3 * i;
+      x[i] = __ldcg(x + i) + (w[q] * __ldcg(u + L.p_idx[q]) + w[q + 1] * __ldcg(u + L.p_idx[q + 1]) +
+                              w[q + 2] * __ldcg(u + L.p_idx[q + 2]));
+    }
+    cluster_sync();
+    for (int it = 0; it < nu_post; ++it)
+      for (int q = 0; q < L.ncolor; ++q) {
+        const int k = post_forward ? q : L.ncolor - 1 - q;
+        cl_rows_any<T>(L, L.cso[k], L.cso[k + 1], 0, cta, red);
+        if (!(l == l0 && it == nu_post - 1 && q == L.ncolor - 1)) cluster_sync();
+      }
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 
 static bool use_pdl() {
@@ -451,6 +617,43 @@ gmg_status launch_coarse(gmg_ctx* c, const T* b, T* x, cudaStream_t s) {
   return launch(k_coarse<T>, (n * 32 + 255) / 256, 256, s, n, (const double*)c->Ainv, b, x);
 }
 
+// The V-cycle below and including level l0: the descending half on one
+// cluster, the coarsest solve on the whole GPU, the ascending half on one
+// cluster.
+template <class T>
+static gmg_status launch_cluster_half(gmg_ctx* c, int l0, int half, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterCTAs);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kClusterCTAs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = use_pdl() ? 2 : 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_cluster_cycle<T>, (const DevLevel*)c->dlv, l0, c->nlev, half,
+                                     c->opt.nu_pre, c->opt.nu_post, c->opt.post_forward);
+  ++g_launches;
+  if (e != cudaSuccess) {
+    set_error(std::string("cluster launch: ") + cudaGetErrorString(e));
+    return GMG_ERR_CUDA;
+  }
+  return GMG_OK;
+}
+
+template <class T>
+static gmg_status launch_cluster(gmg_ctx* c, int l0, cudaStream_t s) {
+  GMG_TRY(launch_cluster_half<T>(c, l0, 0, s));
+  Level& C = c->L[c->nlev - 1];
+  GMG_TRY(launch_coarse<T>(c, Vec<T>::b(C), Vec<T>::x(C), s));
+  return launch_cluster_half<T>(c, l0, 1, s);
+}
+
 // MGI(x_l, b_l, l) of Alg. 2 on the level's own vectors.  x_l holds the
 // initial iterate (zero for every l > 0: the restriction clears it).
 template <class T>
@@ -459,6 +662,7 @@ gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s) {
   T* x = Vec<T>::x(L);
   T* b = Vec<T>::b(L);
   if (l == c->nlev - 1) return launch_coarse<T>(c, b, x, s);
+  if (c->cluster_l0 > 0 && l == c->cluster_l0) return launch_cluster<T>(c, l, s);
   Level& C = c->L[l + 1];
   const bool prof = c->prof && l == 0;
   if (prof) GMG_CK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));

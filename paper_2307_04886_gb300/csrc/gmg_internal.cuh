@@ -130,6 +130,32 @@ struct Level {
   float *X32 = nullptr, *B32 = nullptr, *R32 = nullptr;  // [n x kMaxRhs]
 };
 
+// Device-side descriptor of a level for the persistent small-level kernel.
+constexpr int kClusterCTAs = 8;              // CTAs of the small-level cluster
+constexpr int64_t kClusterMaxRows = 65536;   // levels this small run inside it
+struct DevLevel {
+  int64_t n;
+  int ncolor, lanes;
+  const int64_t* cso;  // first slice of every colour (+ end)
+  int64_t nslice;
+  const int64_t* a_ptr;
+  const int32_t *a_row0, *a_nrow, *a_col;
+  const float* a_v32;
+  const double* a_v64;
+  const float *dinv32, *diag32;
+  const double *dinv64, *diag64;
+  int64_t r_nslice;
+  const int64_t* r_ptr;
+  const int32_t *r_row0, *r_nrow, *r_col;
+  const float* r_v32;
+  const double* r_v64;
+  const int32_t* p_idx;
+  const float* p_w32;
+  const double* p_w64;
+  float *x32, *b32, *r32;
+  double *x64, *b64, *r64;
+};
+
 }  // namespace gmg
 
 struct gmg_ctx {
@@ -144,6 +170,9 @@ struct gmg_ctx {
   double* Winv = nullptr;   // L^-1
   double* Ainv = nullptr;   // A_lambda^-1 (symmetric, full)
   double* dbuf = nullptr;   // diagonal factor blocks, then 1 / L_ii
+  // small levels l >= cluster_l0 run in one cluster kernel (0 = disabled)
+  int cluster_l0 = 0;
+  gmg::DevLevel* dlv = nullptr;
   int* dstatus = nullptr;   // device status words
   // outer iteration (finest level, permuted numbering, FP64)
   double *xs = nullptr, *bs = nullptr, *rs = nullptr, *zs = nullptr, *ps = nullptr, *qs = nullptr, *ros = nullptr;

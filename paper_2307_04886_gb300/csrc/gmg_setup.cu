@@ -1081,6 +1081,57 @@ static gmg_status validate(const gmg_csr* A, int nP, const gmg_prolong* P) {
   return GMG_OK;
 }
 
+// Descriptors of every level for the persistent small-level kernel; the
+// first level with at most kClusterMaxRows rows (below the finest) starts it.
+static gmg_status build_small_level_descriptors(gmg_ctx* c) {
+  // Off by default: measured on GB300 (1M-vertex torus) a cluster phase costs
+  // 3-4 us against about 2 us for a PDL-chained launch.  GMG_CLUSTER_L0=l
+  // starts the cluster kernel at level l.
+  c->cluster_l0 = 0;
+  if (const char* e = std::getenv("GMG_CLUSTER_L0")) c->cluster_l0 = std::atoi(e);
+  if (c->cluster_l0 < 0 || c->cluster_l0 >= c->nlev) c->cluster_l0 = 0;
+  std::vector<DevLevel> d(c->nlev);
+  for (int l = 0; l < c->nlev; ++l) {
+    Level& L = c->L[l];
+    DevLevel& v = d[l];
+    std::memset(&v, 0, sizeof(v));
+    v.n = L.n;
+    v.ncolor = L.ncolor;
+    v.lanes = L.lanes;
+    int64_t* cso;
+    GMG_TRY(upload(c->arena, &cso, L.color_slice_off.data(), L.color_slice_off.size()));
+    v.cso = cso;
+    v.nslice = L.A.nslice;
+    v.a_ptr = L.A.ptr;
+    v.a_row0 = L.A.row0;
+    v.a_nrow = L.A.nrow;
+    v.a_col = L.A.col;
+    v.a_v32 = L.A.v32;
+    v.a_v64 = L.A.v64;
+    v.dinv32 = L.dinv32;
+    v.diag32 = L.diag32;
+    v.dinv64 = L.dinv64;
+    v.diag64 = L.diag64;
+    v.r_nslice = L.R.nslice;
+    v.r_ptr = L.R.ptr;
+    v.r_row0 = L.R.row0;
+    v.r_nrow = L.R.nrow;
+    v.r_col = L.R.col;
+    v.r_v32 = L.R.v32;
+    v.r_v64 = L.R.v64;
+    v.p_idx = L.p_idx;
+    v.p_w32 = L.p_w32;
+    v.p_w64 = L.p_w64;
+    v.x32 = L.x32;
+    v.b32 = L.b32;
+    v.r32 = L.r32;
+    v.x64 = L.x64;
+    v.b64 = L.b64;
+    v.r64 = L.r64;
+  }
+  return upload(c->arena, &c->dlv, d.data(), d.size());
+}
+
 gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P, cudaStream_t s) {
   GMG_TRY(validate(A, nP, P));
   GMG_CK(cudaGetDevice(&c->device));
@@ -1154,6 +1205,7 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   GMG_TRY(a.alloc(&c->red, (size_t)std::max<int64_t>(4 * kRedBlocks, L0.A.nslice / 8 + 64)));
   GMG_TRY(a.alloc(&c->scal, 64));
   GMG_CK(cudaMallocHost((void**)&c->h_scal, 64 * sizeof(double)));
+  GMG_TRY(build_small_level_descriptors(c));
   return numeric_setup(c, s);
 }
 
