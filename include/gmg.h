@@ -193,6 +193,25 @@ gmg_status gmg_coarse_solve(gmg_handle h, int fp32, const double *b, double *x, 
 /* One V-cycle x <- MGI(x, b, 1) of Alg. 2 on the finest level. */
 gmg_status gmg_vcycle(gmg_handle h, int fp32, const double *b, double *x, void *stream);
 
+/* ---- allocation-free residual (no counterpart in the paper) ----
+ * For callers that cannot allocate device memory (code running inside
+ * another framework's memory pool, under an allocator that forbids
+ * cudaMalloc, or where an allocation would synchronise the device): the
+ * FP64 residual r = b - A x of a caller-owned CSR matrix and the norms
+ * norms[0] = ||r||_2, norms[1] = ||b||_2, with no handle and no allocation.
+ * All pointers are device pointers owned by the caller (rowptr n + 1,
+ * col/val rowptr[n], x/b/r n, norms 2 doubles); results are ready when work
+ * queued on `stream` completes.  The block partial sums live in a 1 MiB
+ * static device array that every GPU loading the library keeps until the
+ * process exits, so n is limited to 16,777,216 rows (GMG_ERR_TOO_LARGE
+ * beyond).  The first call on a device looks up that array's device address
+ * (with the device current): make it before any stream capture.  All calls
+ * share the array, so calls that overlap on the GPU (other streams, or
+ * other host threads on the same device) race and must be serialised by the
+ * caller.  Sums run in a fixed order: repeated calls give identical bits. */
+gmg_status gmg_residual_norm_noalloc(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
+                                     const double *x, const double *b, double *r, double *norms, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ EXPORTED = [
     "gmg_default_options", "gmg_status_string", "gmg_last_error", "gmg_setup", "gmg_set_values", "gmg_solve",
     "gmg_solve_batched", "gmg_destroy", "gmg_num_levels", "gmg_level_info", "gmg_level_export", "gmg_smooth",
     "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_coarse_solve", "gmg_vcycle", "gmg_profile",
-    "gmg_profile_read", "gmg_kernel_launches",
+    "gmg_profile_read", "gmg_kernel_launches", "gmg_residual_norm_noalloc",
 ]
 
 
@@ -95,6 +95,7 @@ def load_library(path: str | None = None):
         "gmg_vcycle": (I, [V, I, V, V, V]),
         "gmg_profile": (I, [V, I]),
         "gmg_kernel_launches": (ctypes.c_uint64, []),
+        "gmg_residual_norm_noalloc": (I, [I64, V, V, V, V, V, V, V, V]),
         "gmg_profile_read": (I, [V, V]),
     }
     for name, (res, args) in sig.items():
