@@ -84,6 +84,8 @@ struct Level {
   std::vector<int64_t> rowptr;
   std::vector<int32_t> col;
   int64_t stats[4] = {0, 0, 0, 0};  // fallback rows, repaired columns, single-entry rows, seeds
+  std::vector<int32_t> samples;     // fine index of every coarse point
+  std::vector<int32_t> seed;        // Voronoi cell (coarse index) of every fine point
 };
 
 struct HeapItem {
@@ -330,6 +332,8 @@ Level* build_level(int64_t n, const double* Xp, const int64_t* rp, const int32_t
     for (int s = 0; s < 3; ++s) cnt += L->w[3 * i + s] != 0;
     if (cnt == 1) L->stats[2]++;
   }
+  L->samples = samples;
+  L->seed = seed;
   return L;
 }
 
@@ -355,6 +359,13 @@ void gb_level_copy(void* h, int32_t* idx, double* w, double* Xc, int64_t* rowptr
   std::memcpy(Xc, L->Xc.data(), L->Xc.size() * sizeof(double));
   std::memcpy(rowptr, L->rowptr.data(), L->rowptr.size() * sizeof(int64_t));
   std::memcpy(col, L->col.data(), L->col.size() * sizeof(int32_t));
+}
+
+// Sampled fine points (n_coarse) and the Voronoi cell of every fine point (n).
+void gb_level_cells(void* h, int32_t* samples, int32_t* seed) {
+  Level* L = (Level*)h;
+  std::memcpy(samples, L->samples.data(), L->samples.size() * sizeof(int32_t));
+  std::memcpy(seed, L->seed.data(), L->seed.size() * sizeof(int32_t));
 }
 
 void gb_level_free(void* h) { delete (Level*)h; }

@@ -38,6 +38,7 @@ def _load():
         lib.gb_level_sizes.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.gb_level_copy.argtypes = [ctypes.c_void_p] * 6
         lib.gb_level_free.argtypes = [ctypes.c_void_p]
+        lib.gb_level_cells.argtypes = [ctypes.c_void_p] * 3
         _lib = lib
     return _lib
 
@@ -82,9 +83,14 @@ def build_level(X: np.ndarray, rowptr: np.ndarray, col: np.ndarray, phi: float =
     crp = np.empty(nc + 1, np.int64)
     cci = np.empty(nnz, np.int32)
     lib.gb_level_copy(h, _p(idx), _p(w), _p(Xc), _p(crp), _p(cci))
+    samples = np.empty(nc, np.int32)
+    seed = np.empty(n, np.int32)
+    lib.gb_level_cells(h, _p(samples), _p(seed))
     lib.gb_level_free(h)
     stats = dict(fallback=int(st[0]), repaired=int(st[1]), single=int(st[2]), seeds=int(st[3]))
-    return Prolongation(n, nc, idx, w, stats), Xc, crp, cci
+    P = Prolongation(n, nc, idx, w, stats)
+    P.samples, P.seed = samples, seed
+    return P, Xc, crp, cci
 
 
 def build_hierarchy(X, rowptr, col, phi: float = 1.0 / 8.0, stop: int = 1000, max_levels: int = 24,
