@@ -38,10 +38,26 @@ def compile_oracle(force: bool = False) -> str:
     return _LIB
 
 
-def _load():
+def compile_variant(src_text: str, out_path: str) -> str:
+    """Compiles a modified copy of the oracle source (used by the tests that
+    plant a mistake in the oracle to show that the pins catch it)."""
+    c_path = out_path + ".c"
+    with open(c_path, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-o", out_path,
+                           c_path, "-lm"])
+    return out_path
+
+
+def source_text() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+def _load(path: str | None = None):
     global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(compile_oracle())
+    if path is not None or _lib is None:
+        lib = ctypes.CDLL(path or compile_oracle())
         V = ctypes.c_void_p
         lib.or_create.restype = ctypes.c_int
         lib.or_create.argtypes = [ctypes.c_int64, V, V, V, ctypes.c_int, V, V, V, ctypes.c_int, ctypes.c_int,
@@ -60,6 +76,8 @@ def _load():
         lib.or_mgi.argtypes = [V, ctypes.c_int, V, V]
         lib.or_solve.restype = ctypes.c_int
         lib.or_solve.argtypes = [V, ctypes.c_int, V, V, ctypes.c_double, ctypes.c_int, V, V]
+        if path is not None:
+            return lib
         _lib = lib
     return _lib
 
@@ -82,8 +100,9 @@ class Oracle:
     """The multigrid hierarchy of Alg. 1 for A (scipy CSR) and prolongations
     `Ps` (objects with n_coarse, idx [n,3] int32, w [n,3] float64)."""
 
-    def __init__(self, A: sp.csr_matrix, Ps, nu_pre: int = 2, nu_post: int = 2, post_forward: bool = False):
-        lib = _load()
+    def __init__(self, A: sp.csr_matrix, Ps, nu_pre: int = 2, nu_post: int = 2, post_forward: bool = False,
+                 lib_path: str | None = None):
+        lib = _load(lib_path)
         A = sp.csr_matrix(A)
         A.sort_indices()
         self._keep = []
