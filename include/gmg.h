@@ -149,6 +149,33 @@ gmg_status gmg_solve(gmg_handle h, const double *b, double *x, double tol, int m
 gmg_status gmg_solve_batched(gmg_handle h, int nrhs, const double *B, double *X, double tol, int mem,
                              gmg_solve_info *info, void *stream);
 
+/* ---- A(t) = M + t L kept split (Eq. (smoothing): M lumped mass, L the
+ * Laplacian) and the adjoint gradient of a loss of x = A(t)^-1 M u0 ---- */
+
+/* Like gmg_setup for A = M + t L, remembering M (host, n diagonal entries)
+ * and L (host CSR; every row must store its diagonal; A shares L's pattern).
+ * Errors: those of gmg_setup, and INVALID_ARG for t < 0 or a missing L
+ * diagonal. */
+gmg_status gmg_setup_ML(gmg_handle *h, const double *M_diag, const gmg_csr *L, double t, int n_prolong,
+                        const gmg_prolong *P, const gmg_options *opt, void *stream);
+
+/* Numeric refresh for a new t: A_1 = M + t L on the GPU, then every
+ * Galerkin level and the coarsest factor (as gmg_set_values). */
+gmg_status gmg_set_t(gmg_handle h, double t, void *stream);
+
+/* out = M u (device vectors, caller numbering): the right-hand side M u0 of
+ * Eq. (smoothing). */
+gmg_status gmg_mass(gmg_handle h, const double *u, double *out, void *stream);
+
+/* Gradients of a loss of x = A(t)^-1 M u0, given x and the adjoint
+ * lambda = A(t)^-1 (dloss/dx) (solved with the same hierarchy since A is
+ * symmetric): grad_u0 = M lambda (n), *dLdt = -lambda^T L x (one device
+ * double, summed in a fixed order), and G_vals[k] = -lambda_i x_j for the
+ * k-th stored entry (i, j) of L (dloss/dA on A's pattern).  All device
+ * pointers; any output may be NULL.  Requires a handle from gmg_setup_ML. */
+gmg_status gmg_grad(gmg_handle h, const double *lambda, const double *x, double *grad_u0, double *dLdt,
+                    double *G_vals, void *stream);
+
 /* Releases the handle and its device memory.  NULL is accepted. */
 gmg_status gmg_destroy(gmg_handle h);
 

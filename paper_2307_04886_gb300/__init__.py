@@ -27,7 +27,8 @@ EXPORTED = [
     "gmg_default_options", "gmg_status_string", "gmg_last_error", "gmg_setup", "gmg_set_values", "gmg_solve",
     "gmg_solve_batched", "gmg_destroy", "gmg_num_levels", "gmg_level_info", "gmg_level_export", "gmg_smooth",
     "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_coarse_solve", "gmg_vcycle", "gmg_profile",
-    "gmg_profile_read", "gmg_kernel_launches", "gmg_residual_norm_noalloc",
+    "gmg_profile_read", "gmg_kernel_launches", "gmg_residual_norm_noalloc", "gmg_setup_ML", "gmg_set_t",
+    "gmg_mass", "gmg_grad",
 ]
 
 
@@ -96,6 +97,10 @@ def load_library(path: str | None = None):
         "gmg_profile": (I, [V, I]),
         "gmg_kernel_launches": (ctypes.c_uint64, []),
         "gmg_residual_norm_noalloc": (I, [I64, V, V, V, V, V, V, V, V]),
+        "gmg_setup_ML": (I, [V, V, V, D, I, V, V, V]),
+        "gmg_set_t": (I, [V, D, V]),
+        "gmg_mass": (I, [V, V, V, V]),
+        "gmg_grad": (I, [V, V, V, V, V, V, V]),
         "gmg_profile_read": (I, [V, V]),
     }
     for name, (res, args) in sig.items():
@@ -141,10 +146,16 @@ class Solver:
     """
 
     def __init__(self, A, Ps, precision: int = GMG_FP32_REFINE, nu_pre: int = 2, nu_post: int = 2,
-                 max_iter: int = 100, post_forward: bool = False, use_graphs: bool = True):
+                 max_iter: int = 100, post_forward: bool = False, use_graphs: bool = True, ml=None):
+        """`ml = (Mdiag, L, t)` builds the hierarchy of A = M + t L with M and L
+        kept split (gmg_setup_ML); A is then ignored."""
         import scipy.sparse as sp
 
         lib = load_library()
+        if ml is not None:
+            Mdiag, A, t = ml
+            self._M = np.ascontiguousarray(Mdiag, dtype=np.float64)
+            self.t = float(t)
         A = sp.csr_matrix(A)
         A.sort_indices()
         self.n = A.shape[0]
@@ -163,8 +174,12 @@ class Solver:
         opt = gmg_options(precision, nu_pre, nu_post, max_iter, int(post_forward), int(use_graphs))
         self._opt = opt
         h = ctypes.c_void_p()
-        _check(lib.gmg_setup(ctypes.byref(h), ctypes.byref(csr), len(Ps), arr, ctypes.byref(opt), _stream()),
-               "gmg_setup")
+        if ml is not None:
+            _check(lib.gmg_setup_ML(ctypes.byref(h), _np_ptr(self._M), ctypes.byref(csr), self.t, len(Ps), arr,
+                                    ctypes.byref(opt), _stream()), "gmg_setup_ML")
+        else:
+            _check(lib.gmg_setup(ctypes.byref(h), ctypes.byref(csr), len(Ps), arr, ctypes.byref(opt), _stream()),
+                   "gmg_setup")
         self._h = h
         self._lib = lib
         nl = ctypes.c_int()
@@ -240,6 +255,30 @@ class Solver:
         else:
             v = np.ascontiguousarray(val, dtype=np.float64)
             _check(self._lib.gmg_set_values(self._h, _np_ptr(v), GMG_MEM_HOST, _stream()), "gmg_set_values")
+
+    # ---- A(t) = M + t L and gradients (handles built with ml=...) ----
+    def set_t(self, t: float):
+        _check(self._lib.gmg_set_t(self._h, float(t), _stream()), "gmg_set_t")
+        self.t = float(t)
+
+    def mass(self, u, out=None):
+        import torch
+
+        out = torch.empty_like(u) if out is None else out
+        _check(self._lib.gmg_mass(self._h, _dptr(u, self.n), _dptr(out, self.n), _stream()), "gmg_mass")
+        return out
+
+    def grad(self, lam, x, pattern: bool = False):
+        """(M lam, -lam^T L x as a 0-d tensor, -lam_i x_j on the pattern or None)."""
+        import torch
+
+        g_u0 = torch.empty_like(lam)
+        dldt = torch.zeros((), dtype=torch.float64, device=lam.device)
+        G = torch.empty(self._va.size, dtype=torch.float64, device=lam.device) if pattern else None
+        _check(self._lib.gmg_grad(self._h, _dptr(lam, self.n), _dptr(x, self.n), _dptr(g_u0),
+                                  ctypes.c_void_p(dldt.data_ptr()), _dptr(G) if pattern else None, _stream()),
+               "gmg_grad")
+        return g_u0, dldt, G
 
     def profile(self, enable: bool = True):
         _check(self._lib.gmg_profile(self._h, int(enable)), "gmg_profile")

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
-    "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+    "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-ffp-contract=off",
     "-I", INCLUDE, "-I", CSRC,
 ]
 

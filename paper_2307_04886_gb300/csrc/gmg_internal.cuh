@@ -170,6 +170,12 @@ struct gmg_ctx {
   double* Winv = nullptr;   // L^-1
   double* Ainv = nullptr;   // A_lambda^-1 (symmetric, full)
   double* dbuf = nullptr;   // diagonal factor blocks, then 1 / L_ii
+  // A(t) = M + t L kept split (gmg_setup_ML): lumped mass, L values (caller
+  // CSR order), position of every row's diagonal entry
+  double* ml_M = nullptr;
+  double* ml_L = nullptr;
+  int64_t* ml_dpos = nullptr;
+  double ml_t = 0.0;
   // small levels l >= cluster_l0 run in one cluster kernel (0 = disabled)
   int cluster_l0 = 0;
   gmg::DevLevel* dlv = nullptr;

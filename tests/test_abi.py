@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "gmg.h")
 def declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(gmg_[a-z_0-9]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(gmg_[A-Za-z_0-9]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
