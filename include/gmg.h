@@ -176,6 +176,28 @@ gmg_status gmg_mass(gmg_handle h, const double *u, double *out, void *stream);
 gmg_status gmg_grad(gmg_handle h, const double *lambda, const double *x, double *grad_u0, double *dLdt,
                     double *G_vals, void *stream);
 
+/* ---- many independent systems (meshes of uneven size) in one batch ---- */
+typedef struct gmg_many_ctx *gmg_many;
+
+/* Sets up `nmesh` hierarchies: mesh k has system A[k] and the n_prolong[k]
+ * prolongations P[k][0..] (host arrays, as for gmg_setup).  Errors: those of
+ * gmg_setup for the failing mesh (the message names it). */
+gmg_status gmg_setup_many(gmg_many *m, int nmesh, const gmg_csr *A, const int *n_prolong,
+                          const gmg_prolong *const *P, const gmg_options *opt, void *stream);
+
+/* Solves every mesh's n_k x nrhs system A_k X_k = B_k (row-major, host or
+ * device per `mem`; B[k], X[k] per mesh, X holding the initial guesses) to
+ * ||B - A X||_2 <= tol ||B||_2 per column, with FP32 V-cycles inside FP64
+ * refinement.  Every outer iteration is one CUDA-graph launch in which all
+ * meshes' cycles run concurrently.  info (NULL or nmesh entries) receives the
+ * iteration count and the worst column's relative residual per mesh.
+ * 1 <= nrhs <= 16. */
+gmg_status gmg_solve_many(gmg_many m, int nrhs, const double *const *B, double *const *X, double tol, int mem,
+                          gmg_solve_info *info, void *stream);
+
+/* Releases the batch (NULL accepted). */
+gmg_status gmg_destroy_many(gmg_many m);
+
 /* Releases the handle and its device memory.  NULL is accepted. */
 gmg_status gmg_destroy(gmg_handle h);
 

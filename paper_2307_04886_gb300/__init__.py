@@ -28,7 +28,7 @@ EXPORTED = [
     "gmg_solve_batched", "gmg_destroy", "gmg_num_levels", "gmg_level_info", "gmg_level_export", "gmg_smooth",
     "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_coarse_solve", "gmg_vcycle", "gmg_profile",
     "gmg_profile_read", "gmg_kernel_launches", "gmg_residual_norm_noalloc", "gmg_setup_ML", "gmg_set_t",
-    "gmg_mass", "gmg_grad",
+    "gmg_mass", "gmg_grad", "gmg_setup_many", "gmg_solve_many", "gmg_destroy_many",
 ]
 
 
@@ -101,6 +101,9 @@ def load_library(path: str | None = None):
         "gmg_set_t": (I, [V, D, V]),
         "gmg_mass": (I, [V, V, V, V]),
         "gmg_grad": (I, [V, V, V, V, V, V, V]),
+        "gmg_setup_many": (I, [V, I, V, V, V, V, V]),
+        "gmg_solve_many": (I, [V, I, V, V, D, I, V, V]),
+        "gmg_destroy_many": (I, [V]),
         "gmg_profile_read": (I, [V, V]),
     }
     for name, (res, args) in sig.items():
@@ -326,3 +329,70 @@ class Solver:
     def vcycle(self, x, b, fp32=False):
         _check(self._lib.gmg_vcycle(self._h, int(fp32), _dptr(b), _dptr(x), _stream()), "gmg_vcycle")
         return x
+
+
+class SolverMany:
+    """A batch of independent systems (gmg_setup_many): `systems` is a list
+    of (A, Ps) pairs.  solve() takes one [n_k, nrhs] CUDA float64 tensor per
+    system and solves them all together (one graph launch per iteration)."""
+
+    def __init__(self, systems, precision: int = GMG_FP32_REFINE, nu_pre: int = 2, nu_post: int = 2,
+                 max_iter: int = 100):
+        import scipy.sparse as sp
+
+        lib = load_library()
+        K = len(systems)
+        self._keep = []
+        self.sizes = []
+        csrs = (gmg_csr * K)()
+        nps = (ctypes.c_int * K)()
+        plists = (ctypes.c_void_p * K)()
+        for k, (A, Ps) in enumerate(systems):
+            A = sp.csr_matrix(A)
+            A.sort_indices()
+            rp = np.ascontiguousarray(A.indptr, dtype=np.int64)
+            ci = np.ascontiguousarray(A.indices, dtype=np.int32)
+            va = np.ascontiguousarray(A.data, dtype=np.float64)
+            csrs[k] = gmg_csr(A.shape[0], _np_ptr(rp).value, _np_ptr(ci).value, _np_ptr(va).value)
+            arr = (gmg_prolong * max(1, len(Ps)))()
+            nf = A.shape[0]
+            for l, P in enumerate(Ps):
+                idx = np.ascontiguousarray(P.idx, dtype=np.int32)
+                w = np.ascontiguousarray(P.w, dtype=np.float64)
+                self._keep += [idx, w]
+                arr[l] = gmg_prolong(nf, P.n_coarse, _np_ptr(idx).value, _np_ptr(w).value)
+                nf = P.n_coarse
+            self._keep += [rp, ci, va, arr]
+            nps[k] = len(Ps)
+            plists[k] = ctypes.cast(arr, ctypes.c_void_p).value
+            self.sizes.append(A.shape[0])
+        opt = gmg_options(precision, nu_pre, nu_post, max_iter, 0, 1)
+        h = ctypes.c_void_p()
+        _check(lib.gmg_setup_many(ctypes.byref(h), K, csrs, nps, plists, ctypes.byref(opt), _stream()),
+               "gmg_setup_many")
+        self._h, self._lib, self.K = h, lib, K
+
+    def solve(self, Bs, Xs=None, tol: float = 1e-10, raise_on_fail: bool = True):
+        """Returns (Xs, per-system iterations, per-system relative residual, status)."""
+        import torch
+
+        nrhs = Bs[0].shape[1]
+        Xs = [torch.zeros_like(b) for b in Bs] if Xs is None else Xs
+        bp = (ctypes.c_void_p * self.K)(*[_dptr(b).value for b in Bs])
+        xp = (ctypes.c_void_p * self.K)(*[_dptr(x).value for x in Xs])
+        info = (gmg_solve_info * self.K)()
+        st = self._lib.gmg_solve_many(self._h, nrhs, bp, xp, tol, GMG_MEM_DEVICE, info, _stream())
+        if raise_on_fail:
+            _check(st, "gmg_solve_many")
+        return Xs, [i.iters for i in info], [i.rel_res for i in info], st
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.gmg_destroy_many(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

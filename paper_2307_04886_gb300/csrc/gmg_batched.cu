@@ -464,3 +464,235 @@ extern "C" gmg_status gmg_solve_batched(gmg_handle h, int nrhs, const double* B,
   if (nrhs <= 8) return solve_m<8>(h, nrhs, B, X, tol, mem, info, s);
   return solve_m<16>(h, nrhs, B, X, tol, mem, info, s);
 }
+
+// ------------------------------------------------------------------ many meshes
+// A batch of independent systems (meshes of uneven size), each with its own
+// hierarchy and nrhs right-hand sides.  Every outer iteration is ONE graph
+// launch whose branches run each mesh's multi-right-hand-side FP32 V-cycle,
+// FP64 correction and FP64 residual concurrently; one host synchronisation
+// per iteration reads every mesh's column norms.
+
+struct gmg_many_ctx {
+  std::vector<gmg_handle> h;
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> br;
+  std::vector<cudaEvent_t> ev;
+  cudaGraphExec_t graph[5] = {};  // by NR = 1, 2, 4, 8, 16
+  uint64_t graph_kernels[5] = {};
+};
+
+namespace gmg {
+
+static int nr_slot(int NR) { return NR == 1 ? 0 : NR == 2 ? 1 : NR == 4 ? 2 : NR == 8 ? 3 : 4; }
+
+template <int NR>
+static gmg_status many_graph(gmg_many_ctx* m, cudaGraphExec_t* out, uint64_t* kernels) {
+  const int K = (int)m->h.size();
+  const uint64_t before = g_launches;
+  GMG_CK(cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal));
+  gmg_status st = GMG_OK;
+  cudaError_t e = cudaEventRecord(m->ev[K], m->cap);
+  for (int k = 0; k < K && st == GMG_OK && e == cudaSuccess; ++k) {
+    e = cudaStreamWaitEvent(m->br[k], m->ev[K], 0);
+    if (e == cudaSuccess) st = iteration_m<NR>(m->h[k], m->br[k]);
+    if (st == GMG_OK && e == cudaSuccess) e = cudaEventRecord(m->ev[k], m->br[k]);
+    if (st == GMG_OK && e == cudaSuccess) e = cudaStreamWaitEvent(m->cap, m->ev[k], 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(m->cap, &g);
+  *kernels = g_launches - before;
+  g_launches = before;
+  if (st != GMG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  GMG_CK(e);
+  GMG_CK(ee);
+  cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  GMG_CK(ei);
+  return GMG_OK;
+}
+
+template <int NR>
+static gmg_status many_solve(gmg_many_ctx* m, int nrhs, const double* const* B, double* const* X, double tol,
+                             int mem, gmg_solve_info* info, cudaStream_t s) {
+  const int K = (int)m->h.size();
+  std::vector<std::vector<double>> nb(K, std::vector<double>(NR, 0.0));
+  std::vector<double> rel(K, 0.0);
+  // right-hand sides and initial guesses into every hierarchy's permuted layout
+  for (int k = 0; k < K; ++k) {
+    gmg_ctx* c = m->h[k];
+    Level& L0 = c->L[0];
+    const int64_t n = L0.n;
+    const size_t bytes = sizeof(double) * (size_t)(n * nrhs);
+    const double* bsrc = B[k];
+    if (mem == GMG_MEM_HOST) {
+      GMG_CK(cudaMemcpyAsync(c->RS, B[k], bytes, cudaMemcpyHostToDevice, s));
+      bsrc = c->RS;
+    }
+    k_gather_m<<<gblk(n * NR), 256, 0, s>>>(n, nrhs, NR, L0.perm, bsrc, c->BS);
+    LCK();
+    const double* xsrc = X[k];
+    if (mem == GMG_MEM_HOST) {
+      GMG_CK(cudaMemcpyAsync(c->RS, X[k], bytes, cudaMemcpyHostToDevice, s));
+      xsrc = c->RS;
+    }
+    k_gather_m<<<gblk(n * NR), 256, 0, s>>>(n, nrhs, NR, L0.perm, xsrc, c->XS);
+    LCK();
+    // ||B_c||: the outer residual of a zero iterate
+    double* keep = c->XS;
+    c->XS = c->RS;
+    GMG_CK(cudaMemsetAsync(c->RS, 0, sizeof(double) * (size_t)(n * NR), s));
+    gmg_status st = outer_m<NR>(c, s);
+    c->XS = keep;
+    GMG_TRY(st);
+    GMG_CK(cudaMemcpyAsync(c->h_scal + 8, c->scal + 8, NR * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GMG_CK(cudaStreamSynchronize(s));
+    int zmask = 0;
+    for (int q = 0; q < nrhs; ++q) {
+      nb[k][q] = std::sqrt(c->h_scal[8 + q]);
+      if (nb[k][q] == 0.0) zmask |= 1 << q;
+    }
+    if (zmask) {
+      k_zero_cols<<<gblk(n * NR), 256, 0, s>>>(n, NR, zmask, c->XS);
+      LCK();
+    }
+    GMG_TRY(outer_m<NR>(c, s));
+  }
+  auto fetch = [&]() -> gmg_status {
+    for (int k = 0; k < K; ++k) {
+      gmg_ctx* c = m->h[k];
+      GMG_CK(cudaMemcpyAsync(c->h_scal + 8, c->scal + 8, NR * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    GMG_CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < K; ++k) {
+      double w = 0.0;
+      for (int q = 0; q < nrhs; ++q) {
+        const double r = nb[k][q] > 0 ? std::sqrt(m->h[k]->h_scal[8 + q]) / nb[k][q] : 0.0;
+        w = std::isfinite(r) ? std::max(w, r) : r;
+        if (!std::isfinite(r)) break;
+      }
+      rel[k] = w;
+    }
+    return GMG_OK;
+  };
+  GMG_TRY(fetch());
+  const int slot = nr_slot(NR);
+  int it = 0, max_iter = 0;
+  for (auto* c : m->h) max_iter = std::max(max_iter, c->opt.max_iter);
+  gmg_status st = GMG_ERR_NOT_CONVERGED;
+  auto done = [&]() {
+    for (int k = 0; k < K; ++k)
+      if (!(rel[k] <= tol)) return false;
+    return true;
+  };
+  auto bad = [&]() {
+    for (int k = 0; k < K; ++k)
+      if (!std::isfinite(rel[k])) return true;
+    return false;
+  };
+  if (bad()) st = GMG_ERR_NONFINITE;
+  else if (done()) st = GMG_OK;
+  while (st == GMG_ERR_NOT_CONVERGED && it < max_iter) {
+    if (!m->graph[slot]) GMG_TRY(many_graph<NR>(m, &m->graph[slot], &m->graph_kernels[slot]));
+    GMG_CK(cudaGraphLaunch(m->graph[slot], s));
+    g_launches += m->graph_kernels[slot];
+    ++it;
+    GMG_TRY(fetch());
+    if (bad()) st = GMG_ERR_NONFINITE;
+    else if (done()) st = GMG_OK;
+  }
+  for (int k = 0; k < K; ++k) {
+    gmg_ctx* c = m->h[k];
+    const int64_t n = c->L[0].n;
+    double* dst = mem == GMG_MEM_HOST ? c->RS : X[k];
+    k_scatter_m<<<gblk(n * nrhs), 256, 0, s>>>(n, nrhs, NR, c->L[0].perm, c->XS, dst);
+    LCK();
+    if (mem == GMG_MEM_HOST)
+      GMG_CK(cudaMemcpyAsync(X[k], c->RS, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToHost, s));
+    if (info) {
+      info[k].iters = it;
+      info[k].rel_res = rel[k];
+    }
+  }
+  GMG_CK(cudaStreamSynchronize(s));
+  if (st == GMG_ERR_NOT_CONVERGED) set_error("gmg_solve_many: max_iter reached");
+  if (st == GMG_ERR_NONFINITE) set_error("gmg_solve_many: non-finite residual");
+  return st;
+}
+
+}  // namespace gmg
+
+extern "C" gmg_status gmg_destroy_many(gmg_many m) {
+  if (!m) return GMG_OK;
+  for (auto& g : m->graph)
+    if (g) cudaGraphExecDestroy(g);
+  for (auto e : m->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto s : m->br)
+    if (s) cudaStreamDestroy(s);
+  if (m->cap) cudaStreamDestroy(m->cap);
+  for (auto h : m->h) gmg_destroy(h);
+  delete m;
+  return GMG_OK;
+}
+
+extern "C" gmg_status gmg_setup_many(gmg_many* out, int nmesh, const gmg_csr* A, const int* n_prolong,
+                                     const gmg_prolong* const* P, const gmg_options* opt, void* stream) {
+  if (!out || nmesh < 1 || !A || !n_prolong || !P) {
+    set_error("gmg_setup_many: null argument or nmesh < 1");
+    return GMG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  gmg_many_ctx* m = new gmg_many_ctx();
+  for (int k = 0; k < nmesh; ++k) {
+    gmg_handle h = nullptr;
+    gmg_status st = gmg_setup(&h, &A[k], n_prolong[k], P[k], opt, stream);
+    if (st == GMG_OK) st = ensure_batched(h);
+    if (st != GMG_OK) {
+      std::string keep = gmg_last_error();
+      if (h) gmg_destroy(h);
+      gmg_destroy_many(m);
+      set_error("mesh " + std::to_string(k) + ": " + keep);
+      return st;
+    }
+    m->h.push_back(h);
+  }
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess) set_error(std::string("gmg_setup_many: ") + cudaGetErrorString(e));
+    return e == cudaSuccess;
+  };
+  bool ok = ck(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
+  m->br.assign(nmesh, nullptr);
+  m->ev.assign(nmesh + 1, nullptr);
+  for (int k = 0; ok && k < nmesh; ++k) ok = ck(cudaStreamCreateWithFlags(&m->br[k], cudaStreamNonBlocking));
+  for (int k = 0; ok && k <= nmesh; ++k) ok = ck(cudaEventCreateWithFlags(&m->ev[k], cudaEventDisableTiming));
+  if (!ok) {
+    gmg_destroy_many(m);
+    return GMG_ERR_CUDA;
+  }
+  *out = m;
+  return GMG_OK;
+}
+
+extern "C" gmg_status gmg_solve_many(gmg_many m, int nrhs, const double* const* B, double* const* X, double tol,
+                                     int mem, gmg_solve_info* info, void* stream) {
+  if (!m || !B || !X || nrhs < 1 || nrhs > kMaxRhs || !(tol >= 0.0) ||
+      (mem != GMG_MEM_HOST && mem != GMG_MEM_DEVICE)) {
+    set_error("gmg_solve_many: bad handle, vector list, nrhs (1..16), tolerance or memory kind");
+    return GMG_ERR_INVALID_ARG;
+  }
+  for (size_t k = 0; k < m->h.size(); ++k)
+    if (!B[k] || !X[k]) {
+      set_error("gmg_solve_many: null vector for mesh " + std::to_string(k));
+      return GMG_ERR_INVALID_ARG;
+    }
+  GMG_CK(cudaSetDevice(m->h[0]->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nrhs == 1) return many_solve<1>(m, nrhs, B, X, tol, mem, info, s);
+  if (nrhs == 2) return many_solve<2>(m, nrhs, B, X, tol, mem, info, s);
+  if (nrhs <= 4) return many_solve<4>(m, nrhs, B, X, tol, mem, info, s);
+  if (nrhs <= 8) return many_solve<8>(m, nrhs, B, X, tol, mem, info, s);
+  return many_solve<16>(m, nrhs, B, X, tol, mem, info, s);
+}
