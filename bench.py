@@ -5,9 +5,11 @@ per V-cycle, against the plain FP64 GPU V-cycle.
 
 One step = the numeric hierarchy setup of Alg. 1 for the step's matrix values
 (Galerkin products A_{l+1} = P_l^T A_l P_l, coarsest Cholesky and inverse) and
-the solve from x = 0 to ||b - A x|| <= 1e-10 ||b|| (FP32 V-cycles inside FP64
-iterative refinement).  The hierarchy topology (P_l, colourings, patterns) is
-set up once before timing.  Inputs are resident in HBM when the timed region
+the solve from x = 0 to ||b - A x|| <= 1e-10 ||b|| (FP64 conjugate gradients
+preconditioned by one FP32 V-cycle per iteration).  The plain FP64 V-cycle
+iteration of Alg. 1 and FP32-cycle iterative refinement are timed on the same
+hierarchy and reported beside it.  The hierarchy topology (P_l, colourings,
+patterns, launch shapes) is set up once before timing.  Inputs are resident in HBM when the timed region
 starts; L2 is flushed (256 MB write) before every timed step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmg|reference]
@@ -121,6 +123,17 @@ def gs_launch_bytes(dims, s):
     return sweep / C
 
 
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    of `kernel` on `workload` from the committed ncu capture summary, or None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+        return d.get(workload, {}).get(kernel)
+    except Exception:
+        return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -145,7 +158,7 @@ def run_reference(args):
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         o = oracle.Oracle(s.A, s.Ps)
-        x, iters, hist, ok = o.solve(s.b, tol=1e-10, max_iter=200)
+        x, iters, hist, ok = o.solve(s.b, tol=1e-10, max_iter=200, pcg=True)
         dt = (time.perf_counter() - t0) * 1e3
         del o
         if k >= args.warmup:
@@ -155,10 +168,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "solver": "CPU FP64 oracle: Galerkin setup + stationary V-cycles",
+        "config": {"workload": WORKLOAD_DESC, "solver": "CPU FP64 oracle: Galerkin setup + Cholesky + V-cycle-preconditioned CG",
                    "iterations": iters},
         "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full oracle runs (setup + {iters} V-cycles to 1e-10)"},
+                         "sample": f"{args.steps} full oracle runs (setup + {iters} PCG iterations to 1e-10)"},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -171,11 +184,11 @@ def cpu_baseline(s):
     oracle.compile_oracle()
     t0 = time.perf_counter()
     o = oracle.Oracle(s.A, s.Ps)
-    x, iters, hist, ok = o.solve(s.b, tol=1e-10, max_iter=200)
+    x, iters, hist, ok = o.solve(s.b, tol=1e-10, max_iter=200, pcg=True)
     ms = (time.perf_counter() - t0) * 1e3
     return {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
             "sample": f"one full oracle run on the same system: Galerkin setup + Cholesky + {iters} FP64 "
-                      f"V-cycles to 1e-10, single thread"}
+                      f"V-cycle-preconditioned CG iterations to 1e-10, single thread"}
 
 
 def main():
@@ -211,7 +224,8 @@ def main():
     n = A.shape[0]
 
     t0 = time.perf_counter()
-    solver = g.Solver(A, s.Ps, precision=g.GMG_FP32_REFINE)
+    solver = g.Solver(A, s.Ps, precision=g.GMG_FP32_PCG)
+    lanes = solver.autotune()
     torch.cuda.synchronize()
     symbolic_ms = (time.perf_counter() - t0) * 1e3
     dims = solver.dims
@@ -235,7 +249,7 @@ def main():
         if prof:
             sv.profile(True)
             sv.profile_read()
-        ms, iters, l0 = [], 0, g.kernel_launches()
+        l0 = g.kernel_launches()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         torch.cuda.synchronize()
         w0 = time.perf_counter()
@@ -262,7 +276,7 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
 
-    # breakdown (not part of the headline): numeric setup alone, solve alone
+    # breakdown (not part of the headline): numeric setup alone
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -272,13 +286,14 @@ def main():
     torch.cuda.synchronize()
     setup_ms = e0.elapsed_time(e1) / 5
 
-    # the plain FP64 V-cycle and PCG on the same hierarchy
-    base = g.Solver(A, s.Ps, precision=g.GMG_FP64)
-    fp64_ms, fp64_iters, _, _, fp64_pr, _ = timed(base, max(2, args.steps // 2), 2, prof=True)
-    base.close()
-    pcg = g.Solver(A, s.Ps, precision=g.GMG_FP32_PCG)
-    pcg_ms, pcg_iters, _, _, _, _ = timed(pcg, max(2, args.steps // 2), 2)
-    pcg.close()
+    # the plain FP64 V-cycle and FP32-cycle iterative refinement on the same hierarchy
+    others = {}
+    for name, prec in (("fp64_plain", g.GMG_FP64), ("fp32_refine", g.GMG_FP32_REFINE)):
+        sv = g.Solver(A, s.Ps, precision=prec)
+        sv.autotune()
+        o_ms, o_it, _, _, o_pr, _ = timed(sv, max(2, args.steps // 2), 3, prof=True)
+        others[name] = (o_ms, o_it, o_pr)
+        sv.close()
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     vals_h = torch.tensor(A.data).pin_memory().numpy()
@@ -304,7 +319,10 @@ def main():
     vc_bytes32 = algorithmic_bytes(dims, s.Ps, 4)
     vc_gbs = vc_bytes32 / (cyc_ms / max(cycles, 1) * 1e-3) / 1e9
     vc_bytes64 = algorithmic_bytes(dims, s.Ps, 8)
-    vc64_gbs = vc_bytes64 / (fp64_pr[2] / max(fp64_pr[3], 1) * 1e-3) / 1e9 if fp64_pr else None
+    f_ms, f_it, f_pr = others["fp64_plain"]
+    r_ms, r_it, r_pr = others["fp32_refine"]
+    vc64_us = 1e3 * f_pr[2] / max(f_pr[3], 1)
+    traffic = ncu_traffic("k_gs<float, 1>", WORKLOAD)
 
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -312,26 +330,28 @@ def main():
         "data": "synthetic",
         "config": {
             "workload": WORKLOAD_DESC, "levels": [d[0] for d in dims], "nnz": [d[1] for d in dims],
-            "colours": [d[2] for d in dims], "precision": "FP32 V-cycle (nu=2/2, multicolour GS) in FP64 "
-            "iterative refinement; FP64 coarsest Cholesky", "iterations": iters, "final_rel_res": rr,
+            "colours": [d[2] for d in dims], "warps_per_row": lanes,
+            "precision": "FP64 conjugate gradients preconditioned by one FP32 V-cycle (nu=2/2, multicolour GS) "
+                         "per iteration; FP64 residual, dots and coarsest Cholesky",
+            "iterations": iters, "final_rel_res": rr,
             "step": "numeric Galerkin setup + Cholesky + solve from x=0 to 1e-10",
             "l2": "flushed before every timed step (256 MB write)",
             "numeric_setup_ms": setup_ms, "solve_ms": ms - setup_ms, "symbolic_setup_ms": symbolic_ms,
-            "fp64_plain_ms": fp64_ms, "fp64_plain_iterations": fp64_iters,
-            "fp32_pcg_ms": pcg_ms, "fp32_pcg_iterations": pcg_iters,
-            "speedup_vs_fp64_plain": fp64_ms / ms,
+            "fp64_plain_ms": f_ms, "fp64_plain_iterations": f_it,
+            "fp32_refine_ms": r_ms, "fp32_refine_iterations": r_it,
+            "speedup_vs_fp64_plain": f_ms / ms,
             "vcycle_us_fp32": 1e3 * cyc_ms / max(cycles, 1), "vcycle_gbs_fp32": vc_gbs,
-            "vcycle_bytes_fp32": vc_bytes32,
-            "vcycle_us_fp64": 1e3 * fp64_pr[2] / max(fp64_pr[3], 1) if fp64_pr else None,
-            "vcycle_gbs_fp64": vc64_gbs, "wall_ms_timed_region": wall,
+            "vcycle_bytes_fp32": vc_bytes32, "vcycle_us_fp64": vc64_us,
+            "vcycle_gbs_fp64": vc_bytes64 / (vc64_us * 1e-6) / 1e9, "vcycle_bytes_fp64": vc_bytes64,
+            "wall_ms_timed_region": wall,
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
         },
-        "roofline": {"bound": "hbm", "kernel": "k_gs<float> (finest level, one colour)", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+        "roofline": {"bound": "hbm", "kernel": "k_gs<float, 1> (finest level, one colour)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_launch": gs_bytes, "avg_launch_us": gs_avg_ms * 1e3},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(A.data.nbytes + s.b.nbytes),
                 "d2h_bytes_per_step": int(8 * n)},
-        "gpu_launches": int(round(launches)),
+        "gpu_launches": int(launches),
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

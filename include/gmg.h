@@ -201,6 +201,14 @@ gmg_status gmg_destroy_many(gmg_many m);
 /* Releases the handle and its device memory.  NULL is accepted. */
 gmg_status gmg_destroy(gmg_handle h);
 
+/* Launch-shape autotuner: for every level with Gauss-Seidel sweeps, times
+ * four FP32 sweeps with each row split over G = 1, 2, 4 and 8 warps and keeps
+ * the fastest G (it also serves the residual).  lanes_out (NULL or nlev - 1
+ * ints) receives the choices.  The split changes only the summation order of
+ * a row.  Call between solves; it drops captured graphs (they are re-captured
+ * on the next solve) and overwrites the FP32 work vectors. */
+gmg_status gmg_autotune(gmg_handle h, int *lanes_out, void *stream);
+
 /* ---- kernel timing (measurement support, not part of the method) ----
  * With profiling enabled, gmg_solve records CUDA events on its stream around
  * the finest level's pre- and post-smoothing blocks and around every finest

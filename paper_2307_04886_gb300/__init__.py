@@ -28,7 +28,7 @@ EXPORTED = [
     "gmg_solve_batched", "gmg_destroy", "gmg_num_levels", "gmg_level_info", "gmg_level_export", "gmg_smooth",
     "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_coarse_solve", "gmg_vcycle", "gmg_profile",
     "gmg_profile_read", "gmg_kernel_launches", "gmg_residual_norm_noalloc", "gmg_setup_ML", "gmg_set_t",
-    "gmg_mass", "gmg_grad", "gmg_setup_many", "gmg_solve_many", "gmg_destroy_many",
+    "gmg_mass", "gmg_grad", "gmg_setup_many", "gmg_solve_many", "gmg_destroy_many", "gmg_autotune",
 ]
 
 
@@ -102,6 +102,7 @@ def load_library(path: str | None = None):
         "gmg_mass": (I, [V, V, V, V]),
         "gmg_grad": (I, [V, V, V, V, V, V, V]),
         "gmg_setup_many": (I, [V, I, V, V, V, V, V]),
+        "gmg_autotune": (I, [V, V, V]),
         "gmg_solve_many": (I, [V, I, V, V, D, I, V, V]),
         "gmg_destroy_many": (I, [V]),
         "gmg_profile_read": (I, [V, V]),
@@ -282,6 +283,12 @@ class Solver:
                                   ctypes.c_void_p(dldt.data_ptr()), _dptr(G) if pattern else None, _stream()),
                "gmg_grad")
         return g_u0, dldt, G
+
+    def autotune(self):
+        """Picks the warps-per-row split of every level by timing (gmg_autotune)."""
+        lanes = (ctypes.c_int * max(1, self.nlev - 1))()
+        _check(self._lib.gmg_autotune(self._h, lanes, _stream()), "gmg_autotune")
+        return list(lanes)[: self.nlev - 1]
 
     def profile(self, enable: bool = True):
         _check(self._lib.gmg_profile(self._h, int(enable)), "gmg_profile")

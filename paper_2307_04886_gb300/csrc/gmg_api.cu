@@ -3,7 +3,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <new>
+#include <vector>
 #include <string>
 
 #include "gmg_cycle.cuh"
@@ -159,6 +161,8 @@ gmg_status gmg_setup(gmg_handle* h, const gmg_csr* A, int n_prolong, const gmg_p
   if (!c) return GMG_ERR_OOM;
   if (opt) c->opt = *opt;
   else gmg_default_options(&c->opt);
+  if (const char* e = std::getenv("GMG_NO_GRAPHS"))  // profilers list graph nodes slowly
+    if (e[0] == '1') c->opt.use_graphs = 0;
   if (c->opt.nu_pre < 0 || c->opt.nu_post < 0 || c->opt.max_iter < 0 || c->opt.precision < GMG_FP64 ||
       c->opt.precision > GMG_FP32_PCG) {
     set_error("gmg_setup: invalid options");
@@ -290,6 +294,58 @@ gmg_status gmg_profile_read(gmg_handle h, double* out) {
     h->prof_acc[k] = 0.0;
   }
   return GMG_OK;
+}
+
+gmg_status gmg_autotune(gmg_handle h, int* lanes_out, void* stream) {
+  GMG_TRY(check_handle(h));
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  GMG_CK(cudaEventCreate(&e0));
+  GMG_CK(cudaEventCreate(&e1));
+  gmg_status st = GMG_OK;
+  for (int l = 0; l + 1 < h->nlev && st == GMG_OK; ++l) {
+    Level& L = h->L[l];
+    const int keep = L.lanes;
+    float best_ms = 1e30f;
+    int best = keep;
+    if (cudaMemsetAsync(L.x32, 0, sizeof(float) * (size_t)L.n, s) != cudaSuccess ||
+        cudaMemsetAsync(L.b32, 0, sizeof(float) * (size_t)L.n, s) != cudaSuccess) {
+      st = GMG_ERR_CUDA;
+      break;
+    }
+    for (int G : {1, 2, 4, 8}) {
+      L.lanes = G;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && st == GMG_OK; ++rep) {  // rep 0 warms up
+        cudaEventRecord(e0, s);
+        for (int sweep = 0; sweep < 4 && st == GMG_OK; ++sweep)
+          for (int k = 0; k < L.ncolor && st == GMG_OK; ++k) st = launch_gs_colour<float>(L, k, L.b32, L.x32, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = GMG_ERR_CUDA;
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (st == GMG_OK && ms < best_ms) {
+        best_ms = ms;
+        best = G;
+      }
+    }
+    L.lanes = st == GMG_OK ? best : keep;
+    if (lanes_out) lanes_out[l] = L.lanes;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (auto& g : h->graphs)  // captured cycles hold the old launch shapes
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  if (st == GMG_OK) {  // the small-level descriptors carry the split too
+    std::vector<int> lanes(h->nlev);
+    for (int l = 0; l < h->nlev; ++l) lanes[l] = h->L[l].lanes;
+    for (int l = 0; l < h->nlev; ++l)
+      GMG_CK(cudaMemcpy(&h->dlv[l].lanes, &lanes[l], sizeof(int), cudaMemcpyHostToDevice));
+  }
+  return st;
 }
 
 gmg_status gmg_num_levels(gmg_handle h, int* nlev) {

@@ -529,6 +529,16 @@ __global__ void __launch_bounds__(1024) k_cluster_cycle(const DevLevel* __restri
 
 // ------------------------------------------------------------------ launchers
 
+// Timing events: inside a stream capture they become external event nodes
+// of the graph; outside, plain records.
+static cudaError_t record_timing_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t err = cudaStreamIsCapturing(s, &cs);
+  if (err != cudaSuccess) return err;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(e, s);
+}
+
 static bool use_pdl() {
   static const bool on = [] {
     const char* e = std::getenv("GMG_NO_PDL");
@@ -665,21 +675,21 @@ gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s) {
   if (c->cluster_l0 > 0 && l == c->cluster_l0) return launch_cluster<T>(c, l, s);
   Level& C = c->L[l + 1];
   const bool prof = c->prof && l == 0;
-  if (prof) GMG_CK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
+  if (prof) GMG_CK(record_timing_event(c->ev[0], s));
   for (int it = 0; it < c->opt.nu_pre; ++it)
     for (int k = 0; k < L.ncolor; ++k) GMG_TRY(launch_gs_colour<T>(L, k, b, x, s));
-  if (prof) GMG_CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
+  if (prof) GMG_CK(record_timing_event(c->ev[1], s));
   GMG_TRY(launch_residual<T>(L, x, b, Vec<T>::r(L), s));
   GMG_TRY(launch_restrict<T>(L, Vec<T>::r(L), Vec<T>::b(C), Vec<T>::x(C), s));
   GMG_TRY(vcycle<T>(c, l + 1, s));
   GMG_TRY(launch_prolong<T>(L, Vec<T>::x(C), x, s));
-  if (prof) GMG_CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
+  if (prof) GMG_CK(record_timing_event(c->ev[2], s));
   for (int it = 0; it < c->opt.nu_post; ++it)
     for (int q = 0; q < L.ncolor; ++q) {
       const int k = c->opt.post_forward ? q : L.ncolor - 1 - q;
       GMG_TRY(launch_gs_colour<T>(L, k, b, x, s));
     }
-  if (prof) GMG_CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
+  if (prof) GMG_CK(record_timing_event(c->ev[3], s));
   return GMG_OK;
 }
 
@@ -727,9 +737,9 @@ static gmg_status dot(gmg_ctx* c, int64_t n, const double* a, const double* b, i
 // A finest-level V-cycle, bracketed by timing events when profiling is on.
 template <class T>
 static gmg_status timed_vcycle(gmg_ctx* c, cudaStream_t s) {
-  if (c->prof) GMG_CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
+  if (c->prof) GMG_CK(record_timing_event(c->ev[4], s));
   GMG_TRY(vcycle<T>(c, 0, s));
-  if (c->prof) GMG_CK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
+  if (c->prof) GMG_CK(record_timing_event(c->ev[5], s));
   return GMG_OK;
 }
 
