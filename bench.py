@@ -4,7 +4,7 @@ jittered torus (A = M + 1e-4 L, cotan Laplacian, lumped mass), plus HBM GB/s
 per V-cycle, against the plain FP64 GPU V-cycle.
 
 One step = the numeric hierarchy setup of Alg. 1 for the step's matrix values
-(Galerkin products A_{l+1} = P_l^T A_l P_l, coarsest Cholesky and inverse) and
+(Galerkin products A_{l+1} = P_l^T A_l P_l, the explicit inverse of the coarsest operator) and
 the solve from x = 0 to ||b - A x|| <= 1e-10 ||b|| (FP64 conjugate gradients
 preconditioned by one FP32 V-cycle per iteration).  The plain FP64 V-cycle
 iteration of Alg. 1 and FP32-cycle iterative refinement are timed on the same
@@ -60,11 +60,20 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
+
+    def mark(self, timeout_s: float = 5.0):
+        """Waits for the first sample, then marks the start of the timed region
+        (the last sample before it still counts: it is the state the region
+        starts in)."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.01)
+        self.i0 = max(0, len(self.lines) - 1)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -80,7 +89,7 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[getattr(self, "i0", 0):]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -194,10 +203,15 @@ def cpu_baseline(s):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gmg", choices=["gmg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="set up, autotune, run `warmup` untimed steps and one step, print a short note and exit "
+                         "(the launch sequence a kernel profiler lists; no timing is reported)")
+    ap.add_argument("--lanes", default=None,
+                    help="comma-separated warps-per-row split of every smoothed level (instead of the autotuner)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -225,7 +239,11 @@ def main():
 
     t0 = time.perf_counter()
     solver = g.Solver(A, s.Ps, precision=g.GMG_FP32_PCG)
-    lanes = solver.autotune()
+    if args.lanes:
+        lanes = [int(v) for v in args.lanes.split(",")]
+        solver.set_lanes(lanes)
+    else:
+        lanes = solver.autotune()
     torch.cuda.synchronize()
     symbolic_ms = (time.perf_counter() - t0) * 1e3
     dims = solver.dims
@@ -240,10 +258,12 @@ def main():
         x.zero_()
         return sv.solve(b, x, tol=1e-10)
 
-    def timed(sv, steps, warmup, prof=False):
+    def timed(sv, steps, warmup, prof=False, clk=None):
         for _ in range(warmup):
             step(sv)
         torch.cuda.synchronize()
+        if clk is not None:
+            clk.mark()
         if ws > 1:
             torch.distributed.barrier()
         if prof:
@@ -267,10 +287,22 @@ def main():
             sv.profile(False)
         return sum(ms) / steps, iters, rr, launches, pr, wall
 
+    if args.profile_step:
+        for _ in range(args.warmup + 1):
+            step(solver)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": True, "workload": WORKLOAD, "warps_per_row": lanes,
+                          "kernel_launches_total": g.kernel_launches()}), flush=True)
+        solver.close()
+        return 0
+
     clk = ClockSampler(dev.index)
     clk.start()
-    ms, iters, rr, launches, pr, wall = timed(solver, args.steps, args.warmup, prof=True)
+    ms, iters, rr, launches, _, wall = timed(solver, args.steps, args.warmup, prof=False, clk=clk)
     clocks = clk.stop()
+    # per-kernel timing (CUDA events around the finest smoothing blocks and each
+    # V-cycle) runs the host-driven loop: event nodes cannot sit in the device loop
+    _, _, _, _, pr, _ = timed(solver, 5, 1, prof=True)
     if ws > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -290,8 +322,9 @@ def main():
     others = {}
     for name, prec in (("fp64_plain", g.GMG_FP64), ("fp32_refine", g.GMG_FP32_REFINE)):
         sv = g.Solver(A, s.Ps, precision=prec)
-        sv.autotune()
-        o_ms, o_it, _, _, o_pr, _ = timed(sv, max(2, args.steps // 2), 3, prof=True)
+        sv.set_lanes(lanes)
+        o_ms, o_it, _, _, _, _ = timed(sv, max(2, args.steps // 2), 3)
+        _, _, _, _, o_pr, _ = timed(sv, 3, 1, prof=True)
         others[name] = (o_ms, o_it, o_pr)
         sv.close()
 
@@ -322,7 +355,7 @@ def main():
     f_ms, f_it, f_pr = others["fp64_plain"]
     r_ms, r_it, r_pr = others["fp32_refine"]
     vc64_us = 1e3 * f_pr[2] / max(f_pr[3], 1)
-    traffic = ncu_traffic("k_gs<float, 1>", WORKLOAD)
+    traffic = ncu_traffic(f"k_gs<float, {lanes[0]}>", WORKLOAD)
 
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -332,9 +365,10 @@ def main():
             "workload": WORKLOAD_DESC, "levels": [d[0] for d in dims], "nnz": [d[1] for d in dims],
             "colours": [d[2] for d in dims], "warps_per_row": lanes,
             "precision": "FP64 conjugate gradients preconditioned by one FP32 V-cycle (nu=2/2, multicolour GS) "
-                         "per iteration; FP64 residual, dots and coarsest Cholesky",
+                         "per iteration; FP64 residual, dots and explicit coarsest inverse; the iterations run in a device-side "
+                         "graph loop (conditional WHILE node)",
             "iterations": iters, "final_rel_res": rr,
-            "step": "numeric Galerkin setup + Cholesky + solve from x=0 to 1e-10",
+            "step": "numeric Galerkin setup + coarsest inverse + solve from x=0 to 1e-10",
             "l2": "flushed before every timed step (256 MB write)",
             "numeric_setup_ms": setup_ms, "solve_ms": ms - setup_ms, "symbolic_setup_ms": symbolic_ms,
             "fp64_plain_ms": f_ms, "fp64_plain_iterations": f_it,
@@ -346,7 +380,7 @@ def main():
             "wall_ms_timed_region": wall,
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
         },
-        "roofline": {"bound": "hbm", "kernel": "k_gs<float, 1> (finest level, one colour)", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": f"k_gs<float, {lanes[0]}> (finest level, one colour)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_launch": gs_bytes, "avg_launch_us": gs_avg_ms * 1e3},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(A.data.nbytes + s.b.nbytes),

@@ -69,14 +69,19 @@ def torus_system(n_major: int, n_minor: int, t: float, seed: int, stop: int = 10
     return _mesh_system(f"torus{n_major}x{n_minor}", V, F, t, y, stop=stop)
 
 
-def cloud_system(n: int, k: int = 30, t: float = 1e-3, seed: int = 2, stop: int = 1000):
+def cloud_system(n: int, k: int = 30, t: float = 1e-3, seed: int = 2, stop: int = 1000, graph_k: int = 6):
+    """Point cloud: the system uses the k-nearest-neighbour Gaussian
+    Laplacian; the hierarchy is built on the sparser union graph of the
+    graph_k nearest neighbours, the point-cloud neighbourhood graph of Sec. 4.1
+    (local 1-ring-sized neighbourhoods)."""
     rng = np.random.default_rng(seed)
     P = meshes.noisy_sphere_cloud(n, rng)
     E, h = operators.knn_graph(P, k)
     L = operators.knn_laplacian(P, E, h)
     A = operators.system_matrix(np.ones(n), L, t)
     y = rng.standard_normal(n)
-    rp, ci = operators.edges_to_adjacency(n, E)
+    Eg, _ = operators.knn_graph(P, graph_k)
+    rp, ci = operators.edges_to_adjacency(n, Eg)
     Ps = build_hierarchy(P, rp, ci, stop=stop)
     return System(f"cloud{n}", A, y, Ps, None, L, t, extra=dict(h=h))
 

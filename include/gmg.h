@@ -120,8 +120,10 @@ const char *gmg_last_error(void);
  * P[l].n_fine must equal the size of level l), computes every Galerkin level
  * A_{l+1} = P_l^T A_l P_l on the GPU (two-pass symbolic + numeric product,
  * mirrored to exact symmetry), colours every level (greedy first fit in
- * increasing row index), lays the levels out colour by colour, and factors the
- * coarsest level with a dense FP64 Cholesky.  `opt` may be NULL (defaults).
+ * increasing row index), lays the levels out colour by colour, and forms the
+ * explicit FP64 inverse of the coarsest level (the direct solve of Alg. 2;
+ * block Gauss-Jordan sweeps, every pivot checked positive, which for a
+ * symmetric matrix is the Cholesky criterion).  `opt` may be NULL (defaults).
  * On success *h owns all device memory of the hierarchy; release it with
  * gmg_destroy.  Errors: INVALID_ARG, NOT_SPD, EMPTY_P_COLUMN, CHOLESKY,
  * NONFINITE, TOO_LARGE (coarsest level above 8192 rows, or a Galerkin row with
@@ -208,6 +210,13 @@ gmg_status gmg_destroy(gmg_handle h);
  * a row.  Call between solves; it drops captured graphs (they are re-captured
  * on the next solve) and overwrites the FP32 work vectors. */
 gmg_status gmg_autotune(gmg_handle h, int *lanes_out, void *stream);
+
+/* Sets the warps-per-row split of every level with Gauss-Seidel sweeps
+ * (lanes: nlev - 1 ints, each 1, 2, 4 or 8; GMG_ERR_INVALID_ARG otherwise,
+ * nothing changed).  A fixed choice, e.g. one made earlier by gmg_autotune,
+ * makes the launch sequence independent of timing.  Drops captured graphs
+ * like gmg_autotune; synchronous. */
+gmg_status gmg_set_lanes(gmg_handle h, const int *lanes);
 
 /* ---- kernel timing (measurement support, not part of the method) ----
  * With profiling enabled, gmg_solve records CUDA events on its stream around

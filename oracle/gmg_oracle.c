@@ -23,8 +23,9 @@
  *     colouring in increasing row index; pre-relaxation visits colours in
  *     ascending order, post-relaxation in descending order (a symmetric cycle),
  *     or ascending when `post_forward` is set;
- *   - the Galerkin product is mirrored to exact symmetry: for J > K the entry
- *     (J, K) takes the value computed for (K, J);
+ *   - the Galerkin product adds its terms (P_iJ P_jK) A_ij in a fixed order,
+ *     each with one rounding (C99 fma), and is mirrored to exact symmetry: for
+ *     J > K the entry (J, K) takes the value computed for (K, J);
  *   - the convergence test uses the Euclidean 2-norm and runs after every
  *     cycle (repeat-until); b = 0 returns x = 0 after 0 cycles;
  *   - the coarsest level is solved with a dense Cholesky factorisation.
@@ -104,7 +105,8 @@ static int cmp_i32(const void *a, const void *b) {
 /* Galerkin coarse operator A_c = P^T A P (Alg. 1, build level matrix).
  * Entry (J, K) = sum_i sum_j (P_iJ P_jK) A_ij, accumulated for each coarse row J
  * over the fine rows i of column J of P (ascending), the entries j of row i of
- * A (ascending) and the slots of row j of P, then mirrored to exact symmetry. */
+ * A (ascending) and the slots of row j of P, each term added with a fused
+ * multiply-add (one rounding), then mirrored to exact symmetry. */
 static int galerkin(const olevel *F, olevel *C) {
   int64_t nf = F->n, nc = F->nc;
   /* columns of P: fine rows i with P_iJ != 0, ascending i */
@@ -151,7 +153,7 @@ static int galerkin(const olevel *F, olevel *C) {
           if (wjK == 0.0) continue;
           int32_t K = F->pidx[3 * j + s];
           if (mark[K] != J) { mark[K] = J; acc[K] = 0.0; touched[nt++] = K; }
-          acc[K] += (wiJ * wjK) * a;
+          acc[K] = fma(wiJ * wjK, a, acc[K]);
         }
       }
     }

@@ -28,7 +28,7 @@ EXPORTED = [
     "gmg_solve_batched", "gmg_destroy", "gmg_num_levels", "gmg_level_info", "gmg_level_export", "gmg_smooth",
     "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_coarse_solve", "gmg_vcycle", "gmg_profile",
     "gmg_profile_read", "gmg_kernel_launches", "gmg_residual_norm_noalloc", "gmg_setup_ML", "gmg_set_t",
-    "gmg_mass", "gmg_grad", "gmg_setup_many", "gmg_solve_many", "gmg_destroy_many", "gmg_autotune",
+    "gmg_mass", "gmg_grad", "gmg_setup_many", "gmg_solve_many", "gmg_destroy_many", "gmg_autotune", "gmg_set_lanes",
 ]
 
 
@@ -103,6 +103,7 @@ def load_library(path: str | None = None):
         "gmg_grad": (I, [V, V, V, V, V, V, V]),
         "gmg_setup_many": (I, [V, I, V, V, V, V, V]),
         "gmg_autotune": (I, [V, V, V]),
+        "gmg_set_lanes": (I, [V, V]),
         "gmg_solve_many": (I, [V, I, V, V, D, I, V, V]),
         "gmg_destroy_many": (I, [V]),
         "gmg_profile_read": (I, [V, V]),
@@ -289,6 +290,11 @@ class Solver:
         lanes = (ctypes.c_int * max(1, self.nlev - 1))()
         _check(self._lib.gmg_autotune(self._h, lanes, _stream()), "gmg_autotune")
         return list(lanes)[: self.nlev - 1]
+
+    def set_lanes(self, lanes):
+        """Fixes the warps-per-row split of every smoothed level (gmg_set_lanes)."""
+        arr = (ctypes.c_int * max(1, self.nlev - 1))(*[int(v) for v in lanes])
+        _check(self._lib.gmg_set_lanes(self._h, arr), "gmg_set_lanes")
 
     def profile(self, enable: bool = True):
         _check(self._lib.gmg_profile(self._h, int(enable)), "gmg_profile")

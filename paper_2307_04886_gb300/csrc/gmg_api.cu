@@ -73,6 +73,112 @@ static gmg_status run_cycle_body(gmg_ctx* c, int mode, int seg, cudaStream_t s) 
   return GMG_OK;
 }
 
+// Destroys every captured graph (their launch shapes or event nodes are stale).
+static void drop_graphs(gmg_ctx* c) {
+  for (auto& g : c->graphs)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  for (int m = 0; m < 3; ++m) {
+    if (c->loops[m]) cudaGraphExecDestroy(c->loops[m]);
+    c->loops[m] = nullptr;
+    c->loop_refused[m] = false;
+  }
+}
+
+// Builds the device-side loop of `mode`: a graph holding one conditional
+// WHILE node (condition 1 at every launch) whose body is captured from
+// loop_body.  The body keeps its programmatic launch edges if the driver
+// instantiates them inside a conditional body, else it is captured again in
+// plain stream order; if neither instantiates, the mode keeps the host loop.
+static gmg_status build_loop(gmg_ctx* c, int mode) {
+  if (!c->g_stream) GMG_CK(cudaStreamCreateWithFlags(&c->g_stream, cudaStreamNonBlocking));
+  for (int attempt = 0; attempt < 2 && !c->loops[mode]; ++attempt) {
+    cudaGraph_t g = nullptr;
+    GMG_CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphNodeParams np = {};
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    }
+    if (e == cudaSuccess) {
+      const uint64_t before = g_launches;
+      g_pdl_suspended = attempt == 1;
+      e = cudaStreamBeginCaptureToGraph(c->g_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+      gmg_status st = GMG_OK;
+      if (e == cudaSuccess) {
+        st = loop_body(c, mode, h, c->g_stream);
+        cudaGraph_t body = nullptr;
+        e = cudaStreamEndCapture(c->g_stream, &body);
+      }
+      g_pdl_suspended = false;
+      c->loop_kernels[mode] = g_launches - before;
+      g_launches = before;
+      if (st != GMG_OK) {
+        cudaGraphDestroy(g);
+        return st;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&c->loops[mode], g, 0);
+    }
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->loops[mode] = nullptr;
+    }
+  }
+  if (!c->loops[mode]) c->loop_refused[mode] = true;
+  return GMG_OK;
+}
+
+// Whether the iterations of `mode` run in the device-side loop: graphs on,
+// no per-cycle timing (event nodes are not allowed in a conditional body),
+// GMG_NO_DEVICE_LOOP unset, and the loop graph instantiated.
+static gmg_status device_loop_ready(gmg_ctx* c, int mode, bool* ok) {
+  static const bool off = [] {
+    const char* e = std::getenv("GMG_NO_DEVICE_LOOP");
+    return e && e[0] == '1';
+  }();
+  *ok = false;
+  if (off || !c->opt.use_graphs || c->prof || c->loop_refused[mode]) return GMG_OK;
+  if (!c->loops[mode]) GMG_TRY(build_loop(c, mode));
+  *ok = c->loops[mode] != nullptr;
+  return GMG_OK;
+}
+
+// Runs the device-side loop from iteration *k until k_iter_check stops it;
+// returns the new iteration count in *k, the scalars in h_scal and the
+// loop's residual history in info->history.
+static gmg_status run_loop(gmg_ctx* c, int mode, double tol, int* k, gmg_solve_info* info, cudaStream_t s) {
+  const int it[2] = {*k, c->opt.max_iter};
+  GMG_CK(cudaMemcpyAsync(c->scal + S_TOL, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
+  GMG_CK(cudaMemcpyAsync(c->dloop, it, sizeof(it), cudaMemcpyHostToDevice, s));
+  GMG_CK(cudaGraphLaunch(c->loops[mode], s));
+  int* hk = reinterpret_cast<int*>(c->h_scal + 40);
+  GMG_CK(cudaMemcpyAsync(hk, c->dloop, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GMG_TRY(fetch_scalars(c, s));
+  const int k1 = *hk;
+  if (k1 <= *k || k1 > c->opt.max_iter) {
+    set_error("device loop: iteration counter out of range");
+    return GMG_ERR_CUDA;
+  }
+  g_launches += (uint64_t)(k1 - *k) * c->loop_kernels[mode];
+  if (info && info->history && *k + 1 < info->history_cap) {
+    const int last = std::min(k1, info->history_cap - 1);
+    GMG_CK(cudaMemcpy(info->history + *k + 1, c->dhist + *k + 1, sizeof(double) * (size_t)(last - *k),
+                      cudaMemcpyDeviceToHost));
+  }
+  *k = k1;
+  return GMG_OK;
+}
+
 // Copies an n-vector in caller numbering (host or device) into the permuted
 // device vector `dst` of level l.
 static gmg_status load_vec(gmg_ctx* c, int l, const double* src, int mem, double* dst, double* stage,
@@ -137,8 +243,7 @@ uint64_t gmg_kernel_launches(void) { return g_launches; }
 gmg_status gmg_destroy(gmg_handle h) {
   if (!h) return GMG_OK;
   cudaSetDevice(h->device);
-  for (auto& g : h->graphs)
-    if (g) cudaGraphExecDestroy(g);
+  drop_graphs(h);
   if (h->g_stream) cudaStreamDestroy(h->g_stream);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
@@ -232,10 +337,19 @@ gmg_status gmg_solve(gmg_handle h, const double* b, double* x, double tol, int m
       st = GMG_ERR_NONFINITE;
     } else {
       if (mode == GMG_FP32_PCG) GMG_TRY(pcg_start(c, s));
+      bool fresh = true;  // CG: no step since the (re)start
       while (k < c->opt.max_iter) {
-        GMG_TRY(run_cycle_body(c, mode, 0, s));
-        GMG_TRY(fetch_scalars(c, s));
-        ++k;
+        bool dev = false;
+        if (!(mode == GMG_FP32_PCG && fresh)) GMG_TRY(device_loop_ready(c, mode, &dev));
+        if (dev) {
+          GMG_TRY(run_loop(c, mode, tol, &k, info, s));
+        } else {
+          if (mode == GMG_FP32_PCG && !fresh) GMG_TRY(run_cycle_body(c, mode, 1, s));
+          GMG_TRY(run_cycle_body(c, mode, 0, s));
+          GMG_TRY(fetch_scalars(c, s));
+          ++k;
+        }
+        fresh = false;
         rel = std::sqrt(c->h_scal[S_RR]) / nb;
         if (!std::isfinite(rel)) {
           set_error("gmg_solve: iterate became non-finite");
@@ -252,14 +366,14 @@ gmg_status gmg_solve(gmg_handle h, const double* b, double* x, double tol, int m
             break;
           }
           GMG_TRY(pcg_start(c, s));  // restart from the current iterate
+          fresh = true;
           continue;
         }
-        record(k, rel);
+        if (!dev) record(k, rel);  // the device loop wrote its own history
         if (rel <= tol) {
           st = GMG_OK;
           break;
         }
-        if (mode == GMG_FP32_PCG) GMG_TRY(run_cycle_body(c, mode, 1, s));
       }
       if (st == GMG_ERR_NOT_CONVERGED) set_error("gmg_solve: max_iter reached");
     }
@@ -277,11 +391,7 @@ gmg_status gmg_profile(gmg_handle h, int enable) {
   if ((enable != 0) == h->prof) return GMG_OK;
   if (enable && !h->ev[0])
     for (auto& e : h->ev) GMG_CK(cudaEventCreate(&e));
-  for (auto& g : h->graphs)  // re-capture with or without the event nodes
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
+  drop_graphs(h);  // re-capture with or without the event nodes
   h->prof = enable != 0;
   h->prof_pending = false;
   return GMG_OK;
@@ -293,6 +403,13 @@ gmg_status gmg_profile_read(gmg_handle h, double* out) {
     out[k] = h->prof_acc[k];
     h->prof_acc[k] = 0.0;
   }
+  return GMG_OK;
+}
+
+// Makes a new warps-per-row choice take effect: captured cycles hold the old
+// launch shapes.
+static gmg_status apply_lanes(gmg_handle h) {
+  drop_graphs(h);
   return GMG_OK;
 }
 
@@ -334,18 +451,24 @@ gmg_status gmg_autotune(gmg_handle h, int* lanes_out, void* stream) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  for (auto& g : h->graphs)  // captured cycles hold the old launch shapes
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
-  if (st == GMG_OK) {  // the small-level descriptors carry the split too
-    std::vector<int> lanes(h->nlev);
-    for (int l = 0; l < h->nlev; ++l) lanes[l] = h->L[l].lanes;
-    for (int l = 0; l < h->nlev; ++l)
-      GMG_CK(cudaMemcpy(&h->dlv[l].lanes, &lanes[l], sizeof(int), cudaMemcpyHostToDevice));
-  }
+  if (st == GMG_OK) st = apply_lanes(h);
   return st;
+}
+
+gmg_status gmg_set_lanes(gmg_handle h, const int* lanes) {
+  GMG_TRY(check_handle(h));
+  if (!lanes) {
+    set_error("gmg_set_lanes: null lanes");
+    return GMG_ERR_INVALID_ARG;
+  }
+  for (int l = 0; l + 1 < h->nlev; ++l)
+    if (lanes[l] != 1 && lanes[l] != 2 && lanes[l] != 4 && lanes[l] != 8) {
+      set_error("gmg_set_lanes: level " + std::to_string(l) + " split " + std::to_string(lanes[l]) +
+                " is not 1, 2, 4 or 8");
+      return GMG_ERR_INVALID_ARG;
+    }
+  for (int l = 0; l + 1 < h->nlev; ++l) h->L[l].lanes = lanes[l];
+  return apply_lanes(h);
 }
 
 gmg_status gmg_num_levels(gmg_handle h, int* nlev) {

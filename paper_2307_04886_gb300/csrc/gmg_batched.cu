@@ -340,10 +340,13 @@ static gmg_status ensure_batched(gmg_ctx* c) {
   GMG_TRY(c->arena.alloc(&c->XS, (size_t)n * kMaxRhs));
   GMG_TRY(c->arena.alloc(&c->BS, (size_t)n * kMaxRhs));
   GMG_TRY(c->arena.alloc(&c->RS, (size_t)n * kMaxRhs));
-  const int64_t need = (int64_t)nblk(c->L[0].A.nslice * 32) * kMaxRhs + 64;
+  // per-column partials of the batched residual, and never smaller than the
+  // single-vector partials the buffer already serves
+  const int64_t need = std::max<int64_t>((int64_t)nblk(c->L[0].A.nslice * 32) * kMaxRhs + 64, c->red_cap);
   double* red2;
-  GMG_TRY(c->arena.alloc(&red2, (size_t)std::max<int64_t>(need, 4 * kRedBlocks)));
+  GMG_TRY(c->arena.alloc(&red2, (size_t)need));
   c->red = red2;
+  c->red_cap = need;
   return GMG_OK;
 }
 

@@ -13,7 +13,7 @@
 // atomics, a fixed summation order); it also clears the coarse iterate (the
 // recursive call of Alg. 2 starts from zero).  The prolongation reads three
 // packed (index, weight) slots per fine row.  The coarsest level applies the
-// explicit inverse of its FP64 Cholesky factor as a warp-per-row GEMV.
+// explicit FP64 inverse of its operator as a warp-per-row GEMV.
 //
 // Launches use programmatic dependent launch: a kernel may start while its
 // predecessor drains; it loads only setup-time data (matrix values, column
@@ -25,14 +25,13 @@
 #include <cmath>
 #include <cstdlib>
 #include <string>
+#include <type_traits>
 #include <utility>
 
 #include "gmg_cycle.cuh"
 
 namespace gmg {
 
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ------------------------------------------------------------------ kernels
 
@@ -324,36 +323,104 @@ __global__ void k_reduce_final(int count, const double* partial, double* out) {
   if (threadIdx.x == 0) *out = red[0];
 }
 
-// PCG scalars live on the device: sc[2] = r.z, sc[3] = p.Ap, sc[4] = Polak-
-// Ribiere numerator z.(r - r_old).
-__global__ void k_pcg_axpy(int64_t n, const double* sc, const double* p, const double* q, double* x, double* r,
-                           double* rold) {
+// PCG scalars live on the device (slots S_*): r.z, p.Ap, the Polak-Ribiere
+// numerator z.(r - r_old), beta.
+//
+// Block sums in the fixed order of k_dot_partial (same grid, same per-thread
+// ranges, same tree), so the fused kernels below give the same bits as a
+// separate dot product.
+__device__ __forceinline__ void block_sum_store(double v, double* red, double* out) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// alpha = rz / pq; r_old = r; x += alpha p; r -= alpha q; partial sums of
+// r.r; and the FP32 right-hand side of the next preconditioning cycle
+// (b32 = r, x32 = 0).  Grid: kRedBlocks x 256.
+__global__ void __launch_bounds__(256) k_pcg_axpy(int64_t n, const double* sc, const double* p, const double* q,
+                                                  double* x, double* r, double* rold, float* b32, float* x32,
+                                                  double* __restrict__ partial) {
+  __shared__ double red[256];
   pdl_wait();
   pdl_trigger();
-  const double alpha = sc[2] / sc[3];
-  GRID_LOOP(i, n) {
+  const double alpha = sc[S_RZ] / sc[S_PQ];
+  double rr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
     const double ri = r[i];
     rold[i] = ri;
     x[i] += alpha * p[i];
-    r[i] = ri - alpha * q[i];
+    const double rn = ri - alpha * q[i];
+    r[i] = rn;
+    b32[i] = (float)rn;
+    x32[i] = 0.f;
+    rr += rn * rn;
+  }
+  block_sum_store(rr, red, partial + blockIdx.x);
+}
+
+// z = (double) x32 (the preconditioned residual); partial sums of
+// z.(r - r_old) into partial[0 .. gridDim) and of r.z into
+// partial[gridDim .. 2 gridDim).  Grid: kRedBlocks x 256.
+__global__ void __launch_bounds__(256) k_pcg_zdots(int64_t n, const float* x32, const double* r, const double* rold,
+                                                   double* __restrict__ partial) {
+  __shared__ double red[256];
+  pdl_wait();
+  pdl_trigger();
+  double num = 0.0, rz = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+    const double zi = (double)x32[i], ri = r[i];
+    num += zi * (ri - rold[i]);
+    rz += ri * zi;
+  }
+  block_sum_store(num, red, partial + blockIdx.x);
+  block_sum_store(rz, red, partial + gridDim.x + blockIdx.x);
+}
+
+// Final sums of k_pcg_zdots (the tree of k_reduce_final): beta = num / rz_old,
+// then rz = r.z for the next iteration.
+__global__ void k_pcg_beta(int count, const double* partial, double* sc) {
+  __shared__ double red[256];
+  pdl_wait();
+  pdl_trigger();
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < count; i += 256) {
+    a += partial[i];
+    b += partial[count + i];
+  }
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double num = red[0];
+  __syncthreads();
+  red[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double rzn = red[0];
+    sc[S_NUM] = num;
+    sc[S_BETA] = num / sc[S_RZ];
+    sc[S_RZN] = rzn;
+    sc[S_RZ] = rzn;
   }
 }
-__global__ void k_pcg_dir(int64_t n, const double* sc, const double* z, double* p) {
+
+// p = z + beta p with z = (double) x32.
+__global__ void k_pcg_dir(int64_t n, const double* sc, const float* x32, double* p) {
   pdl_wait();
   pdl_trigger();
-  const double beta = sc[4] / sc[2];
-  GRID_LOOP(i, n) p[i] = z[i] + beta * p[i];
-}
-__global__ void k_copy_scalar(const double* src, double* dst) {
-  pdl_wait();
-  pdl_trigger();
-  *dst = *src;
-}
-// d = r - rold (for the Polak-Ribiere numerator)
-__global__ void k_sub(int64_t n, const double* a, const double* b, double* d) {
-  pdl_wait();
-  pdl_trigger();
-  GRID_LOOP(i, n) d[i] = a[i] - b[i];
+  const double beta = sc[S_BETA];
+  GRID_LOOP(i, n) p[i] = (double)x32[i] + beta * p[i];
 }
 __global__ void k_copy(int64_t n, const double* a, double* b) {
   pdl_wait();
@@ -361,37 +428,23 @@ __global__ void k_copy(int64_t n, const double* a, double* b) {
   GRID_LOOP(i, n) b[i] = a[i];
 }
 
-// ------------------------------------------------------------------ small levels
-// The levels at and below `l0` (all small) run as one persistent kernel per
-// V-cycle on a single thread-block cluster: every colour phase, residual,
-// restriction, coarse solve and prolongation of those levels is separated
-// by a hardware cluster barrier instead of a kernel boundary.  Vectors are
-// read through L2 (ld.global.cg): they are written by other CTAs of the
-// cluster between barriers.  Matrix data is setup-time data.
+// ------------------------------------------------------------------ tail of the FP32 cycle
+// The smoothed levels l0 .. lambda-1 whose vectors fit in shared memory and
+// the coarsest level run in one launch on one thread-block cluster of ncta
+// CTAs.  Every CTA keeps full copies of x, r, b, 1/a_ii and a_ii of each tail
+// level (and x, b of the coarsest level) in its shared memory, plus the
+// sliced-ELL entries of the slices it owns: slice s of colour range
+// [s0, s1) belongs to CTA (s - s0) mod ncta.  A phase (one Gauss-Seidel
+// colour, the residual, the restriction, the coarsest GEMV, the
+// prolongation) updates the rows the CTA owns and stores every new value into
+// all CTAs' copies through distributed shared memory; a cluster barrier
+// (release / acquire) ends the phase.  So a phase costs a hardware barrier
+// rather than a kernel boundary, and reads global memory only for the
+// restriction and prolongation weights and the coarsest inverse.  Rows of one
+// colour are never adjacent, so a colour phase reads only values that no CTA
+// writes during it.  All CTAs run the same sequence of barriers.
 
-template <class T> struct DV;
-template <> struct DV<float> {
-  __device__ static const float* av(const DevLevel& L) { return L.a_v32; }
-  __device__ static const float* dinv(const DevLevel& L) { return L.dinv32; }
-  __device__ static const float* diag(const DevLevel& L) { return L.diag32; }
-  __device__ static const float* rv(const DevLevel& L) { return L.r_v32; }
-  __device__ static const float* pw(const DevLevel& L) { return L.p_w32; }
-  __device__ static float* x(const DevLevel& L) { return L.x32; }
-  __device__ static float* b(const DevLevel& L) { return L.b32; }
-  __device__ static float* r(const DevLevel& L) { return L.r32; }
-};
-template <> struct DV<double> {
-  __device__ static const double* av(const DevLevel& L) { return L.a_v64; }
-  __device__ static const double* dinv(const DevLevel& L) { return L.dinv64; }
-  __device__ static const double* diag(const DevLevel& L) { return L.diag64; }
-  __device__ static const double* rv(const DevLevel& L) { return L.r_v64; }
-  __device__ static const double* pw(const DevLevel& L) { return L.p_w64; }
-  __device__ static double* x(const DevLevel& L) { return L.x64; }
-  __device__ static double* b(const DevLevel& L) { return L.b64; }
-  __device__ static double* r(const DevLevel& L) { return L.r64; }
-};
-
-__device__ __forceinline__ void cluster_sync() {
+__device__ __forceinline__ void tail_sync() {
   __syncwarp();
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -400,131 +453,162 @@ __device__ __forceinline__ unsigned cluster_rank() {
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
   return r;
 }
-
-// One Gauss-Seidel colour (mode 0) or the residual over all slices (mode 1)
-// of level L, split over the cluster: G warps of one CTA share a slice.
-template <class T, int G>
-__device__ void cl_rows(const DevLevel& L, int64_t s0, int64_t s1, int mode, int cta, T (&red)[32][33]) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, part = warp % G;
-  constexpr int SPC = 32 / G;                 // slices per CTA per round
-  constexpr int SPR = SPC * kClusterCTAs;     // slices per round
-  const int64_t rounds = (s1 - s0 + SPR - 1) / SPR;
-  const T* val = DV<T>::av(L);
-  T* x = DV<T>::x(L);
-  const T* b = DV<T>::b(L);
-  for (int64_t rd = 0; rd < rounds; ++rd) {
-    const int64_t s = s0 + rd * SPR + (int64_t)cta * SPC + warp / G;
-    const RowPart p = row_part<G>(s, s1, L.a_ptr, L.a_row0, L.a_nrow, part, lane);
-    // all matrix loads first, then all gathers: two dependent round trips per row
-    T pv[kPrefetch];
-    int pc[kPrefetch];
-    prefetch_row<T, G>(p, L.a_col, val, pv, pc);
-    T xv[kPrefetch];
-#pragma unroll
-    for (int q = 0; q < kPrefetch; ++q) xv[q] = q < p.nk ? __ldcg(x + pc[q]) : T(0);
-    T acc = 0;
-#pragma unroll
-    for (int q = 0; q < kPrefetch; ++q) acc += pv[q] * xv[q];
-    for (int q = kPrefetch; q < p.nk; ++q) {
-      const int64_t e = p.e + (int64_t)q * G * 32;
-      acc += val[e] * __ldcg(x + L.a_col[e]);
-    }
-    if constexpr (G > 1) {
-      red[warp][lane] = acc;
-      __syncthreads();
-      if (part == 0) {
-#pragma unroll
-        for (int g = 1; g < G; ++g) acc += red[warp + g][lane];
-      }
-    }
-    if (part == 0 && p.active) {
-      if (mode == 0) {
-        x[p.row] = (__ldcg(b + p.row) - acc) * DV<T>::dinv(L)[p.row];
-      } else {
-        DV<T>::r(L)[p.row] = __ldcg(b + p.row) - (acc + DV<T>::diag(L)[p.row] * __ldcg(x + p.row));
-      }
-    }
-    if constexpr (G > 1) __syncthreads();
+// Stores v at the same shared-memory location in every CTA of the cluster.
+__device__ __forceinline__ void tail_bcast(float* p, float v, int ncta) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  for (int r = 0; r < ncta; ++r) {
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(r));
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
   }
 }
 
-template <class T>
-__device__ void cl_rows_any(const DevLevel& L, int64_t s0, int64_t s1, int mode, int cta, T (&red)[32][33]) {
-  switch (L.lanes) {
-    case 1: cl_rows<T, 1>(L, s0, s1, mode, cta, red); break;
-    case 2: cl_rows<T, 2>(L, s0, s1, mode, cta, red); break;
-    case 4: cl_rows<T, 4>(L, s0, s1, mode, cta, red); break;
-    default: cl_rows<T, 8>(L, s0, s1, mode, cta, red); break;
-  }
+template <class U>
+__device__ __forceinline__ U* sm_at(char* sm, int off) {
+  return reinterpret_cast<U*>(sm + off);
 }
 
-// half 0: pre-smoothing, residual and restriction of levels l0 .. lambda-1
-// (down to the coarsest right-hand side); half 1: prolongation and
-// post-smoothing from lambda-1 back up to l0.  The coarsest solve between
-// the halves runs on the whole GPU (its FP64 GEMV needs every SM's FP64 pipe).
-template <class T>
-__global__ void __launch_bounds__(1024) k_cluster_cycle(const DevLevel* __restrict__ lv, int l0, int nlev, int half,
-                                                        int nu_pre, int nu_post, int post_forward) {
-  __shared__ T red[32][33];
-  const int cta = (int)cluster_rank();
+// One Gauss-Seidel colour (mode 0), the residual of one colour's rows
+// (mode 1) or the prolongation into one colour's rows (mode 2, from the
+// next level's x in xn) over the owned slices of colour k.
+__device__ void tail_rows(const TailLevel& L, char* sm, int k, int mode, const float* xn, int cta, int ncta) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gwarp = cta * 32 + warp;                         // warp index in the cluster
-  const int64_t gthread = (int64_t)cta * 1024 + threadIdx.x;  // thread index in the cluster
-  constexpr int kWarps = 32 * kClusterCTAs;
-  constexpr int kThreads = 1024 * kClusterCTAs;
-  pdl_wait();
+  const int* cso = sm_at<int>(sm, L.o_cso);
+  const int s0 = cso[k], s1 = cso[k + 1];
+  float* x = sm_at<float>(sm, L.o_x);
+  const float* b = sm_at<float>(sm, L.o_b);
+  const int* row0 = sm_at<int>(sm, L.o_row0);
+  const int* nrow = sm_at<int>(sm, L.o_nrow);
+  const int* width = sm_at<int>(sm, L.o_width);
+  const int* soff = sm_at<int>(sm, L.o_soff);
+  const float* val = sm_at<float>(sm, L.o_val);
+  const int* col = sm_at<int>(sm, L.o_col);
+  const int nw = blockDim.x >> 5;
+  for (int s = s0 + cta + warp * ncta; s < s1; s += nw * ncta) {
+    const int row = row0[s] + lane;
+    const bool active = lane < nrow[s];
+    if (mode == 2) {
+      if (active) {
+        const int q = 3 * row;
+        const float v = x[row] + (L.p_w32[q] * xn[L.p_idx[q]] + L.p_w32[q + 1] * xn[L.p_idx[q + 1]] +
+                                  L.p_w32[q + 2] * xn[L.p_idx[q + 2]]);
+        tail_bcast(x + row, v, ncta);
+      }
+      continue;
+    }
+    const int w = width[s], off = soff[s] + lane;
+    float acc = 0.f;
+    for (int q = 0; q < w; ++q) acc += val[off + q * 32] * x[col[off + q * 32]];
+    if (!active) continue;
+    if (mode == 0)
+      tail_bcast(x + row, (b[row] - acc) * sm_at<float>(sm, L.o_dinv)[row], ncta);
+    else
+      tail_bcast(sm_at<float>(sm, L.o_r) + row, b[row] - (acc + sm_at<float>(sm, L.o_diag)[row] * x[row]), ncta);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_tail_cycle(const __grid_constant__ TailDesc D) {
+  extern __shared__ __align__(16) char sm[];
+  const int cta = (int)cluster_rank(), ncta = D.ncta;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  // load everything of the tail that is read during the phases
+  for (int t = 0; t < D.ntail; ++t) {
+    const TailLevel& L = D.lv[t];
+    for (int i = tid; i < L.n; i += nt) {
+      sm_at<float>(sm, L.o_dinv)[i] = L.dinv32[i];
+      sm_at<float>(sm, L.o_diag)[i] = L.diag32[i];
+    }
+    for (int s = tid; s < L.nslice; s += nt) {
+      sm_at<int>(sm, L.o_row0)[s] = L.a_row0[s];
+      sm_at<int>(sm, L.o_nrow)[s] = L.a_nrow[s];
+      sm_at<int>(sm, L.o_width)[s] = (int)((L.a_ptr[s + 1] - L.a_ptr[s]) >> 5);
+      sm_at<int>(sm, L.o_soff)[s] = L.soff[s];
+    }
+    for (int k = tid; k <= L.ncolor; k += nt) sm_at<int>(sm, L.o_cso)[k] = L.cso[k];
+    // owned slices' entries, one warp per slice
+    for (int k = 0; k < L.ncolor; ++k)
+      for (int s = L.cso[k] + cta + warp * ncta; s < L.cso[k + 1]; s += nw * ncta) {
+        const int64_t e0 = L.a_ptr[s], ne = L.a_ptr[s + 1] - e0;
+        const int o = L.soff[s];
+        for (int64_t e = lane; e < ne; e += 32) {
+          sm_at<float>(sm, L.o_val)[o + e] = L.a_v32[e0 + e];
+          sm_at<int>(sm, L.o_col)[o + e] = L.a_col[e0 + e];
+        }
+      }
+  }
+  pdl_wait();  // the vectors below are written by the previous kernel
   pdl_trigger();
-  if (half == 0) {
-    for (int l = l0; l < nlev - 1; ++l) {
-      const DevLevel& L = lv[l];
-      for (int it = 0; it < nu_pre; ++it)
-        for (int k = 0; k < L.ncolor; ++k) {
-          cl_rows_any<T>(L, L.cso[k], L.cso[k + 1], 0, cta, red);
-          cluster_sync();
-        }
-      cl_rows_any<T>(L, 0, L.nslice, 1, cta, red);
-      cluster_sync();
-      // restriction into level l+1 (clears its iterate)
-      const DevLevel& C = lv[l + 1];
-      const T* r = DV<T>::r(L);
-      const T* rw = DV<T>::rv(L);
-      for (int64_t s = gwarp; s < L.r_nslice; s += kWarps) {
-        if (lane >= L.r_nrow[s]) continue;
-        const int64_t e0 = L.r_ptr[s] + lane;
-        const int wd = (int)((L.r_ptr[s + 1] - L.r_ptr[s]) >> 5);
-        T acc = 0;
-#pragma unroll 8
-        for (int k = 0; k < wd; ++k) {
-          const int64_t e = e0 + (int64_t)k * 32;
-          acc += rw[e] * __ldcg(r + L.r_col[e]);
-        }
-        const int64_t row = L.r_row0[s] + lane;
-        DV<T>::b(C)[row] = acc;
-        DV<T>::x(C)[row] = T(0);
-      }
-      if (l + 1 < nlev - 1) cluster_sync();
+  {
+    const TailLevel& L = D.lv[0];
+    for (int i = tid; i < L.n; i += nt) {
+      sm_at<float>(sm, L.o_x)[i] = L.x32[i];
+      sm_at<float>(sm, L.o_b)[i] = L.b32[i];
     }
-    return;
   }
-  for (int l = nlev - 2; l >= l0; --l) {
-    const DevLevel& L = lv[l];
-    const DevLevel& C = lv[l + 1];
-    T* x = DV<T>::x(L);
-    const T* u = DV<T>::x(C);
-    const T* w = DV<T>::pw(L);
-    for (int64_t i = gthread; i < L.n; i += kThreads) {
-      const int64_t q = 3 * i;
-      x[i] = __ldcg(x + i) + (w[q] * __ldcg(u + L.p_idx[q]) + w[q + 1] * __ldcg(u + L.p_idx[q + 1]) +
-                              w[q + 2] * __ldcg(u + L.p_idx[q + 2]));
+  __syncthreads();
+  tail_sync();
+  // down: smoothing, residual, restriction
+  for (int t = 0; t < D.ntail; ++t) {
+    const TailLevel& L = D.lv[t];
+    for (int it = 0; it < D.nu_pre; ++it)
+      for (int k = 0; k < L.ncolor; ++k) {
+        tail_rows(L, sm, k, 0, nullptr, cta, ncta);
+        tail_sync();
+      }
+    for (int k = 0; k < L.ncolor; ++k) tail_rows(L, sm, k, 1, nullptr, cta, ncta);
+    tail_sync();
+    // restriction: b_next = P^T r over the owned slices of the transpose; the
+    // next iterate starts from zero (each CTA clears its own copy)
+    const bool last = t + 1 == D.ntail;
+    float* bn = last ? sm_at<float>(sm, D.o_bc) : sm_at<float>(sm, D.lv[t + 1].o_b);
+    float* xn = last ? sm_at<float>(sm, D.o_xc) : sm_at<float>(sm, D.lv[t + 1].o_x);
+    const int nn = last ? D.nc : D.lv[t + 1].n;
+    for (int i = tid; i < nn; i += nt) xn[i] = 0.f;
+    const float* r = sm_at<float>(sm, L.o_r);
+    for (int s = cta + warp * ncta; s < L.r_nslice; s += nw * ncta) {
+      if (lane >= L.r_nrow[s]) continue;
+      const int64_t e0 = L.r_ptr[s] + lane;
+      const int wd = (int)((L.r_ptr[s + 1] - L.r_ptr[s]) >> 5);
+      float acc = 0.f;
+      for (int q = 0; q < wd; ++q) acc += L.r_v32[e0 + (int64_t)q * 32] * r[L.r_col[e0 + (int64_t)q * 32]];
+      tail_bcast(bn + L.r_row0[s] + lane, acc, ncta);
     }
-    cluster_sync();
-    for (int it = 0; it < nu_post; ++it)
+    tail_sync();
+  }
+  // coarsest: x_c = A^-1 b_c, one warp per row
+  {
+    const float* bc = sm_at<float>(sm, D.o_bc);
+    float* xc = sm_at<float>(sm, D.o_xc);
+    for (int J = cta + warp * ncta; J < D.nc; J += nw * ncta) {
+      const float* a = D.ainv32 + (int64_t)J * D.nc;
+      float acc = 0.f;
+      for (int K = lane; K < D.nc; K += 32) acc += a[K] * bc[K];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) tail_bcast(xc + J, acc, ncta);
+    }
+    tail_sync();
+  }
+  // up: prolongation and post-smoothing
+  for (int t = D.ntail - 1; t >= 0; --t) {
+    const TailLevel& L = D.lv[t];
+    const float* xn = t + 1 == D.ntail ? sm_at<float>(sm, D.o_xc) : sm_at<float>(sm, D.lv[t + 1].o_x);
+    for (int k = 0; k < L.ncolor; ++k) tail_rows(L, sm, k, 2, xn, cta, ncta);
+    tail_sync();
+    for (int it = 0; it < D.nu_post; ++it)
       for (int q = 0; q < L.ncolor; ++q) {
-        const int k = post_forward ? q : L.ncolor - 1 - q;
-        cl_rows_any<T>(L, L.cso[k], L.cso[k + 1], 0, cta, red);
-        if (!(l == l0 && it == nu_post - 1 && q == L.ncolor - 1)) cluster_sync();
+        tail_rows(L, sm, D.post_forward ? q : L.ncolor - 1 - q, 0, nullptr, cta, ncta);
+        tail_sync();
       }
   }
+  // the owned rows of the first tail level back to global memory
+  const TailLevel& L = D.lv[0];
+  const int* cso = sm_at<int>(sm, L.o_cso);
+  for (int k = 0; k < L.ncolor; ++k)
+    for (int s = cso[k] + cta + warp * ncta; s < cso[k + 1]; s += nw * ncta)
+      if (lane < sm_at<int>(sm, L.o_nrow)[s]) {
+        const int row = sm_at<int>(sm, L.o_row0)[s] + lane;
+        L.x32[row] = sm_at<float>(sm, L.o_x)[row];
+      }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -537,36 +621,6 @@ static cudaError_t record_timing_event(cudaEvent_t e, cudaStream_t s) {
   if (err != cudaSuccess) return err;
   return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
                                              : cudaEventRecord(e, s);
-}
-
-static bool use_pdl() {
-  static const bool on = [] {
-    const char* e = std::getenv("GMG_NO_PDL");
-    return !(e && e[0] == '1');
-  }();
-  return on;
-}
-
-// Launches `k` on `s` with programmatic stream serialisation.
-template <typename... P, typename... A>
-static gmg_status launch(void (*k)(P...), int64_t grid, int block, cudaStream_t s, A&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)std::max<int64_t>(1, grid));
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = use_pdl() ? 1 : 0;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
-  ++g_launches;
-  if (e != cudaSuccess) {
-    set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
-    return GMG_ERR_CUDA;
-  }
-  return GMG_OK;
 }
 
 static inline int64_t blocks_for(int64_t threads, int per = 256, int64_t cap = 152 * 64) {
@@ -627,41 +681,56 @@ gmg_status launch_coarse(gmg_ctx* c, const T* b, T* x, cudaStream_t s) {
   return launch(k_coarse<T>, (n * 32 + 255) / 256, 256, s, n, (const double*)c->Ainv, b, x);
 }
 
-// The V-cycle below and including level l0: the descending half on one
-// cluster, the coarsest solve on the whole GPU, the ascending half on one
-// cluster.
-template <class T>
-static gmg_status launch_cluster_half(gmg_ctx* c, int l0, int half, cudaStream_t s) {
+// The tail of an FP32 cycle (levels tail_l0 .. lambda) as one cluster launch.
+static gmg_status launch_tail(gmg_ctx* c, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kClusterCTAs);
+  cfg.gridDim = dim3(c->tail.ncta);
   cfg.blockDim = dim3(1024);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = (size_t)c->tail_smem;
   cfg.stream = s;
   cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kClusterCTAs;
+  at[0].val.clusterDim.x = c->tail.ncta;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = use_pdl() ? 2 : 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_cluster_cycle<T>, (const DevLevel*)c->dlv, l0, c->nlev, half,
-                                     c->opt.nu_pre, c->opt.nu_post, c->opt.post_forward);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_tail_cycle, c->tail);
   ++g_launches;
   if (e != cudaSuccess) {
-    set_error(std::string("cluster launch: ") + cudaGetErrorString(e));
+    set_error(std::string("tail cluster launch: ") + cudaGetErrorString(e));
     return GMG_ERR_CUDA;
   }
   return GMG_OK;
 }
 
-template <class T>
-static gmg_status launch_cluster(gmg_ctx* c, int l0, cudaStream_t s) {
-  GMG_TRY(launch_cluster_half<T>(c, l0, 0, s));
-  Level& C = c->L[c->nlev - 1];
-  GMG_TRY(launch_coarse<T>(c, Vec<T>::b(C), Vec<T>::x(C), s));
-  return launch_cluster_half<T>(c, l0, 1, s);
+gmg_status tail_configure(gmg_ctx* c, int ncta, int smem, bool* ok) {
+  *ok = false;
+  if (cudaFuncSetAttribute(k_tail_cycle, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+      cudaFuncSetAttribute(k_tail_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmemLimit) != cudaSuccess) {
+    cudaGetLastError();
+    return GMG_OK;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ncta);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = ncta;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_tail_cycle, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return GMG_OK;
+  }
+  *ok = nclusters >= 1;
+  return GMG_OK;
 }
 
 // MGI(x_l, b_l, l) of Alg. 2 on the level's own vectors.  x_l holds the
@@ -672,7 +741,8 @@ gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s) {
   T* x = Vec<T>::x(L);
   T* b = Vec<T>::b(L);
   if (l == c->nlev - 1) return launch_coarse<T>(c, b, x, s);
-  if (c->cluster_l0 > 0 && l == c->cluster_l0) return launch_cluster<T>(c, l, s);
+  if constexpr (std::is_same<T, float>::value)
+    if (c->tail_l0 > 0 && l == c->tail_l0) return launch_tail(c, s);
   Level& C = c->L[l + 1];
   const bool prof = c->prof && l == 0;
   if (prof) GMG_CK(record_timing_event(c->ev[0], s));
@@ -724,6 +794,11 @@ gmg_status launch_f2d(int64_t n, const float* a, double* b, cudaStream_t s) {
 // rs = bs - A xs (FP64, finest level) and scal[slot] = ||rs||^2.
 static gmg_status outer_residual(gmg_ctx* c, int slot, cudaStream_t s) {
   Level& L = c->L[0];
+  const int64_t blocks = (L.A.nslice + (8 / L.lanes) - 1) / (8 / L.lanes);
+  if (blocks > c->red_cap) {
+    set_error("outer residual: more blocks than reduction partials");
+    return GMG_ERR_TOO_LARGE;
+  }
   int64_t nb = 0;
   GMG_TRY(launch_residual_p<double>(L, c->xs, c->bs, c->rs, c->red, s, &nb));
   return launch(k_reduce_final, 1, 256, s, (int)nb, (const double*)c->red, c->scal + slot);
@@ -772,19 +847,23 @@ gmg_status iteration_body(gmg_ctx* c, int mode, int seg, cudaStream_t s) {
   }
   if (seg == 0) {
     const int64_t nb = (L.A.nslice * 32 + 255) / 256;
+    if (nb > c->red_cap) {
+      set_error("PCG: more blocks than reduction partials");
+      return GMG_ERR_TOO_LARGE;
+    }
     GMG_TRY(launch(k_spmv_dot, nb, 256, s, L.A.nslice, L.A.ptr, L.A.row0, L.A.nrow, L.A.col, L.A.v64, L.diag64,
                    (const double*)c->ps, c->qs, c->red));
     GMG_TRY(launch(k_reduce_final, 1, 256, s, (int)nb, (const double*)c->red, c->scal + S_PQ));
-    GMG_TRY(launch(k_pcg_axpy, blocks_for(n), 256, s, n, (const double*)c->scal, (const double*)c->ps,
-                   (const double*)c->qs, c->xs, c->rs, c->ros));
-    return dot(c, n, c->rs, c->rs, S_RR, s);
+    GMG_TRY(launch(k_pcg_axpy, kRedBlocks, 256, s, n, (const double*)c->scal, (const double*)c->ps,
+                   (const double*)c->qs, c->xs, c->rs, c->ros, L.b32, L.x32, c->red));
+    return launch(k_reduce_final, 1, 256, s, kRedBlocks, (const double*)c->red, c->scal + S_RR);
   }
-  GMG_TRY(precond32(c, c->rs, c->zs, s));
-  GMG_TRY(launch(k_sub, blocks_for(n), 256, s, n, (const double*)c->rs, (const double*)c->ros, c->qs));
-  GMG_TRY(dot(c, n, c->zs, c->qs, S_NUM, s));
-  GMG_TRY(dot(c, n, c->rs, c->zs, S_RZN, s));
-  GMG_TRY(launch(k_pcg_dir, blocks_for(n), 256, s, n, (const double*)c->scal, (const double*)c->zs, c->ps));
-  return launch(k_copy_scalar, 1, 1, s, (const double*)(c->scal + S_RZN), c->scal + S_RZ);
+  // b32 = r and x32 = 0 were set by segment 0
+  GMG_TRY(timed_vcycle<float>(c, s));
+  GMG_TRY(launch(k_pcg_zdots, kRedBlocks, 256, s, n, (const float*)L.x32, (const double*)c->rs,
+                 (const double*)c->ros, c->red));
+  GMG_TRY(launch(k_pcg_beta, 1, 256, s, kRedBlocks, (const double*)c->red, c->scal));
+  return launch(k_pcg_dir, blocks_for(n), 256, s, n, (const double*)c->scal, (const float*)L.x32, c->ps);
 }
 
 // PCG start: z = MGI32(0, r), rz = r.z, p = z (r must be current).
@@ -793,6 +872,26 @@ gmg_status pcg_start(gmg_ctx* c, cudaStream_t s) {
   GMG_TRY(precond32(c, c->rs, c->zs, s));
   GMG_TRY(dot(c, n, c->rs, c->zs, S_RZ, s));
   return launch(k_copy, blocks_for(n), 256, s, n, (const double*)c->zs, c->ps);
+}
+
+// Convergence test of the device-side loop, one thread: advances the
+// iteration counter it[0], records rel = ||r|| / ||b|| (same arithmetic as the
+// host test) and keeps the loop going while rel is finite, above the
+// tolerance and the counter below it[1].
+__global__ void k_iter_check(const double* sc, int* it, double* hist, cudaGraphConditionalHandle h) {
+  pdl_wait();
+  pdl_trigger();
+  const int k = ++it[0];
+  const double rel = sqrt(sc[S_RR]) / sqrt(sc[S_NB2]);
+  hist[k] = rel;
+  const bool go = isfinite(rel) && !(rel <= sc[S_TOL]) && k < it[1];
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+gmg_status loop_body(gmg_ctx* c, int mode, cudaGraphConditionalHandle h, cudaStream_t s) {
+  if (mode == GMG_FP32_PCG) GMG_TRY(iteration_body(c, mode, 1, s));
+  GMG_TRY(iteration_body(c, mode, 0, s));
+  return launch(k_iter_check, 1, 1, s, (const double*)c->scal, c->dloop, c->dhist, h);
 }
 
 gmg_status outer_residual_norm(gmg_ctx* c, cudaStream_t s) { return outer_residual(c, S_RR, s); }

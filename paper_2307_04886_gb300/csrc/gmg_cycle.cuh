@@ -43,7 +43,11 @@ gmg_status iteration_body(gmg_ctx* c, int mode, int seg, cudaStream_t s);
 gmg_status pcg_start(gmg_ctx* c, cudaStream_t s);
 gmg_status outer_residual_norm(gmg_ctx* c, cudaStream_t s);
 gmg_status norm_b(gmg_ctx* c, cudaStream_t s);
-enum { S_NB2 = 0, S_RR = 1, S_RZ = 2, S_PQ = 3, S_NUM = 4, S_RZN = 5 };
+enum { S_NB2 = 0, S_RR = 1, S_RZ = 2, S_PQ = 3, S_NUM = 4, S_RZN = 5, S_BETA = 6, S_TOL = 7 };
+// One iteration of the device-side loop (PCG: segment 1 of the previous
+// iteration, then segment 0) followed by the convergence test that sets the
+// loop's condition `h` (captured into the body of a WHILE node).
+gmg_status loop_body(gmg_ctx* c, int mode, cudaGraphConditionalHandle h, cudaStream_t s);
 gmg_status launch_gather(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t s);
 gmg_status launch_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t s);
 

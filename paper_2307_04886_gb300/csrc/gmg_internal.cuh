@@ -2,8 +2,11 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "gmg.h"
@@ -48,6 +51,45 @@ extern thread_local uint64_t g_launches;
     if (s_ != GMG_OK) return s_;          \
   } while (0)
 
+// Programmatic dependent launch: a kernel may start while its predecessor
+// drains; `pdl_wait` blocks until the predecessor grid has completed and its
+// writes are visible, `pdl_trigger` lets the successor start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// GMG_NO_PDL=1 turns programmatic dependent launch off (plain stream order);
+// g_pdl_suspended turns it off for the launches of the calling thread.
+extern thread_local bool g_pdl_suspended;
+inline bool use_pdl() {
+  static const bool on = [] {
+    const char* e = std::getenv("GMG_NO_PDL");
+    return !(e && e[0] == '1');
+  }();
+  return on && !g_pdl_suspended;
+}
+
+// Launches `k` on `s` with programmatic stream serialisation.
+template <typename... P, typename... A>
+inline gmg_status launch(void (*k)(P...), int64_t grid, int block, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)std::max<int64_t>(1, grid));
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = use_pdl() ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+  ++g_launches;
+  if (e != cudaSuccess) {
+    set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
+    return GMG_ERR_CUDA;
+  }
+  return GMG_OK;
+}
+
 // Device allocation registry of a handle: everything is freed by gmg_destroy.
 struct Arena {
   std::vector<void*> ptrs;
@@ -66,6 +108,15 @@ struct Arena {
   void release() {
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();
+  }
+  void release_one(void* p) {
+    for (auto& q : ptrs)
+      if (q == p) {
+        cudaFree(q);
+        q = ptrs.back();
+        ptrs.pop_back();
+        return;
+      }
   }
 };
 
@@ -105,6 +156,15 @@ struct Level {
   int32_t* plan_edge = nullptr;
   double* plan_coef = nullptr;
   int64_t plan_terms = 0;
+  // the same plan sliced for the numeric pass (entries with terms, sorted by
+  // term count, 32 per slice, terms stored [k][lane], zero-padded)
+  int64_t plan_nup = 0;
+  int64_t plan_long_slices = 0;  // leading slices whose width exceeds 32 terms
+  int32_t* plan_up = nullptr;
+  int32_t* plan_mirror = nullptr;  // CSR position of each entry's mirror, -1 on the diagonal
+  int64_t* plan_sptr = nullptr;
+  int32_t* plan_sedge = nullptr;
+  double* plan_scoef = nullptr;
   // off-diagonal part of A_l in the permuted numbering
   Ell A;
   double* diag64 = nullptr;
@@ -130,30 +190,38 @@ struct Level {
   float *X32 = nullptr, *B32 = nullptr, *R32 = nullptr;  // [n x kMaxRhs]
 };
 
-// Device-side descriptor of a level for the persistent small-level kernel.
-constexpr int kClusterCTAs = 8;              // CTAs of the small-level cluster
-constexpr int64_t kClusterMaxRows = 65536;   // levels this small run inside it
-struct DevLevel {
-  int64_t n;
-  int ncolor, lanes;
-  const int64_t* cso;  // first slice of every colour (+ end)
-  int64_t nslice;
+// The tail of an FP32 V-cycle (the smoothed levels l0 .. lambda-1 and the
+// coarsest level) runs as one launch on one thread-block cluster; these are
+// its descriptors (passed by value).  Offsets are bytes into the dynamic
+// shared memory of every CTA (the same layout in each).
+constexpr int kMaxTail = 4;            // smoothed levels in the tail
+constexpr int kTailSmemLimit = 200 * 1024;
+struct TailLevel {
+  int n, ncolor, nslice, r_nslice;
+  // shared-memory copies: x, r, b, 1/a_ii, a_ii (all rows); per slice: first
+  // row, rows, width, offset of its entries in the owner's arrays; colour
+  // slice offsets; the owned slices' values and columns
+  int o_x, o_r, o_b, o_dinv, o_diag, o_row0, o_nrow, o_width, o_soff, o_cso, o_val, o_col;
   const int64_t* a_ptr;
   const int32_t *a_row0, *a_nrow, *a_col;
-  const float* a_v32;
-  const double* a_v64;
-  const float *dinv32, *diag32;
-  const double *dinv64, *diag64;
-  int64_t r_nslice;
+  const float *a_v32, *dinv32, *diag32;
+  const int32_t* soff;  // offset of each slice's entries in its owner CTA's arrays
+  const int32_t* cso;   // first slice of every colour (+ end)
+  // restriction into the next level (sliced ELL over its rows) and
+  // prolongation from it (three slots per row of this level)
   const int64_t* r_ptr;
   const int32_t *r_row0, *r_nrow, *r_col;
   const float* r_v32;
-  const double* r_v64;
   const int32_t* p_idx;
   const float* p_w32;
-  const double* p_w64;
-  float *x32, *b32, *r32;
-  double *x64, *b64, *r64;
+  float *x32, *b32;  // global vectors of this level (the first tail level reads x, b and writes x)
+};
+struct TailDesc {
+  int ntail, nc, ncta;
+  int nu_pre, nu_post, post_forward;
+  int o_xc, o_bc;        // shared-memory copies of the coarsest x and b
+  const float* ainv32;   // coarsest inverse, FP32, nc x nc
+  TailLevel lv[kMaxTail];
 };
 
 }  // namespace gmg
@@ -166,19 +234,21 @@ struct gmg_ctx {
   gmg::Arena arena;
   // coarsest level
   int64_t nco = 0;
-  double* dense = nullptr;  // n x n work / Cholesky factor
-  double* Winv = nullptr;   // L^-1
-  double* Ainv = nullptr;   // A_lambda^-1 (symmetric, full)
-  double* dbuf = nullptr;   // diagonal factor blocks, then 1 / L_ii
+  double* dense = nullptr;  // npad x npad sweep work matrix (npad = n rounded up to 32)
+  double* Ainv = nullptr;   // A_lambda^-1 (symmetric, full, n x n)
+  double* dbuf = nullptr;   // two 32 x 32 pivot inverses, panel U and U D^-1 (npad x 32 each)
+  int* gj_cnt = nullptr;    // per-sweep arrival counters of the next pivot tile
   // A(t) = M + t L kept split (gmg_setup_ML): lumped mass, L values (caller
   // CSR order), position of every row's diagonal entry
   double* ml_M = nullptr;
   double* ml_L = nullptr;
   int64_t* ml_dpos = nullptr;
   double ml_t = 0.0;
-  // small levels l >= cluster_l0 run in one cluster kernel (0 = disabled)
-  int cluster_l0 = 0;
-  gmg::DevLevel* dlv = nullptr;
+  // FP32 cycles run levels >= tail_l0 as one cluster launch (0 = off)
+  int tail_l0 = 0;
+  int tail_smem = 0;
+  gmg::TailDesc tail{};
+  float* Ainv32 = nullptr;  // coarsest inverse in FP32 for the tail launch
   int* dstatus = nullptr;   // device status words
   // outer iteration (finest level, permuted numbering, FP64)
   double *xs = nullptr, *bs = nullptr, *rs = nullptr, *zs = nullptr, *ps = nullptr, *qs = nullptr, *ros = nullptr;
@@ -188,11 +258,19 @@ struct gmg_ctx {
   double* RS = nullptr;    // batched FP64 residual
   double* BS = nullptr;
   double* red = nullptr;   // reduction partials
+  int64_t red_cap = 0;     // capacity of `red` in doubles
   double* scal = nullptr;  // device scalars (norms, dots)
   double* h_scal = nullptr;  // pinned host mirror
   // captured iteration bodies, indexed by mode * 2 + segment
   cudaGraphExec_t graphs[8] = {};
   uint64_t graph_kernels[8] = {};  // kernel nodes of each captured graph
+  // device-side outer loop per mode: a graph whose conditional WHILE node
+  // repeats the iteration until the convergence test fails on the device
+  cudaGraphExec_t loops[3] = {};
+  uint64_t loop_kernels[3] = {};  // kernel nodes of one loop iteration
+  bool loop_refused[3] = {};      // instantiation failed: the host loop serves the mode
+  int* dloop = nullptr;           // device iteration counter, iteration limit
+  double* dhist = nullptr;        // relative residual per iteration (max_iter + 1)
   cudaStream_t g_stream = nullptr;
   bool values_ready = false;
   // kernel timing: events bracket the finest level's smoothing blocks
@@ -202,3 +280,9 @@ struct gmg_ctx {
   cudaEvent_t ev[6] = {};
   double prof_acc[4] = {0, 0, 0, 0};  // smoothing ms, GS launches, cycle ms, cycles
 };
+
+namespace gmg {
+// Whether a tail cluster of ncta CTAs with `smem` bytes of shared memory each
+// can be scheduled on the device (sets the kernel's attributes).
+gmg_status tail_configure(gmg_ctx* c, int ncta, int smem, bool* ok);
+}  // namespace gmg

@@ -170,7 +170,7 @@ gmg_status gmg_grad(gmg_handle h, const double* lambda, const double* x, double*
   }
   if (dLdt || G_vals) {
     const int nb = (int)((n + 255) / 256);
-    if (nb > (int)std::max<int64_t>(4 * kRedBlocks, L0.A.nslice / 8 + 64)) {
+    if (nb > h->red_cap) {
       set_error("gmg_grad: reduction scratch too small");
       return GMG_ERR_TOO_LARGE;
     }

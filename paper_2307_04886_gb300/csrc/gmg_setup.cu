@@ -1,4 +1,4 @@
-// Setup of the multigrid hierarchy (Alg. 1, lines "build level matrix"):
+// Setup of the multigrid hierarchy (the level-matrix steps of Alg. 1):
 //  * validation of A and P_l (host);
 //  * Galerkin product A_{l+1} = P_l^T A_l P_l on the GPU: a symbolic pass
 //    (per-row hash sets in shared memory: count, scan, sorted fill) and a
@@ -6,7 +6,8 @@
 //    symmetry (the entry below the diagonal takes the value above it);
 //  * greedy colouring and colour-major renumbering (host, integer work);
 //  * sliced-ELL layout of every level and of every restriction P_l^T;
-//  * dense FP64 Cholesky of the coarsest level and its explicit inverse.
+//  * explicit FP64 inverse of the coarsest level (the direct solve of
+//    Alg. 2 at the coarsest level) by block sweeps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +23,7 @@ namespace gmg {
 
 thread_local std::string g_last_error;
 thread_local uint64_t g_launches = 0;
+thread_local bool g_pdl_suspended = false;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
 // ------------------------------------------------------------------ device
@@ -373,38 +375,101 @@ __global__ void __launch_bounds__(kPlanWarps * 32)
   }
 }
 
-// Numeric pass: value of every entry = sum over its plan of coef * A_l value,
-// multiplied and added with separate roundings in plan order.
-__global__ void __launch_bounds__(256)
-    k_gal_apply(int64_t nnz, const int64_t* __restrict__ plan_ptr, const int32_t* __restrict__ plan_edge,
-                const double* __restrict__ plan_coef, const double* __restrict__ a_val, double* __restrict__ c_val) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int64_t t = plan_ptr[e]; t < plan_ptr[e + 1]; ++t)
-      acc = __dadd_rn(acc, __dmul_rn(plan_coef[t], a_val[plan_edge[t]]));
-    c_val[e] = acc;
+// The plan re-laid for the numeric pass: the entries on or above the
+// diagonal, sorted by their number of terms (descending), in slices of 32;
+// slice g stores its terms [k][lane] (term k of the slice's lane-th entry at
+// sptr[g] + 32 k + lane), padded with zero coefficients.  A thread per entry
+// then reads its terms with the warp's loads contiguous, and still adds them
+// in the entry's canonical order.
+__global__ void k_plan_slice(int64_t nup, const int32_t* __restrict__ up_entry, const int64_t* __restrict__ plan_ptr,
+                             const int32_t* __restrict__ plan_edge, const double* __restrict__ plan_coef,
+                             const int64_t* __restrict__ sptr, int32_t* __restrict__ sedge,
+                             double* __restrict__ scoef) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nup; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = i >> 5, lane = i & 31;
+    const int64_t e = up_entry[i];
+    const int64_t t0 = plan_ptr[e], nt = plan_ptr[e + 1] - t0;
+    const int64_t width = (sptr[g + 1] - sptr[g]) >> 5;
+    for (int64_t k = 0; k < width; ++k) {
+      const int64_t dst = sptr[g] + k * 32 + lane;
+      sedge[dst] = k < nt ? plan_edge[t0 + k] : 0;
+      scoef[dst] = k < nt ? plan_coef[t0 + k] : 0.0;
+    }
   }
 }
 
-// Exact symmetry: entry (J, K) with K < J takes the value of (K, J).
-__global__ void k_gal_mirror(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                             double* __restrict__ val) {
-  for (int64_t J = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; J < n; J += (int64_t)gridDim.x * blockDim.x) {
-    for (int64_t k = rp[J]; k < rp[J + 1]; ++k) {
-      const int32_t K = col[k];
-      if (K >= J) break;
-      int64_t lo = rp[K], hi = rp[K + 1] - 1;
-      while (lo <= hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        const int32_t cm = col[mid];
-        if (cm < J) lo = mid + 1;
-        else if (cm > J) hi = mid - 1;
-        else {
-          val[k] = val[mid];
-          break;
+// Writes the value x of Galerkin entry e (on or above the diagonal) and of
+// its mirror m (below it; m < 0 on the diagonal) into the level's CSR and
+// solve layout: sliced-ELL slot (FP64 and FP32) or diagonal with its
+// reciprocal.  err bit 0: a diagonal entry <= 0; bit 1: a non-finite value.
+__device__ __forceinline__ void emit_entry(int64_t e, int64_t m, double x, double* __restrict__ c_val,
+                                           const int64_t* __restrict__ csr2ell, double* __restrict__ e64,
+                                           float* __restrict__ e32, double* __restrict__ d64,
+                                           float* __restrict__ d32, double* __restrict__ di64,
+                                           float* __restrict__ di32, int* __restrict__ err) {
+  if (!isfinite(x)) atomicOr(err, 2);
+  c_val[e] = x;
+  const int64_t se = csr2ell[e];
+  if (se >= 0) {
+    e64[se] = x;
+    e32[se] = (float)x;
+  } else {
+    const int64_t r = -1 - se;
+    if (!(x > 0.0)) atomicOr(err, 1);
+    d64[r] = x;
+    d32[r] = (float)x;
+    di64[r] = 1.0 / x;
+    di32[r] = (float)(1.0 / x);
+  }
+  if (m >= 0) {
+    c_val[m] = x;
+    const int64_t sm = csr2ell[m];
+    e64[sm] = x;
+    e32[sm] = (float)x;
+  }
+}
+
+// Numeric pass of one Galerkin level, one thread per entry on or above the
+// diagonal (sliced plan order, slices [g0, g1)): value = sum over its terms
+// of coef * A_l value, each term added with one fused multiply-add in the
+// plan's order (zero padding adds +0), then written with its mirror (exact
+// symmetry) into the CSR and the solve layout.  Terms are loaded B at a time
+// before they are added, so a long term list is not a chain of dependent
+// loads: B = 32 for the slices of long entries (hundreds of terms on coarse
+// levels), B = 8 elsewhere (fewer registers, more warps in flight).
+constexpr int kGalThreads = 64;  // small blocks: coarse levels have few entries, and each SM's FP64 pipe counts
+constexpr int kGalLongWidth = 32;  // slices wider than this take the B = 32 kernel
+template <int B>
+__global__ void __launch_bounds__(kGalThreads)
+    k_gal_level(int64_t g0, int64_t g1, const int32_t* __restrict__ up_entry, const int32_t* __restrict__ mirror,
+                const int64_t* __restrict__ sptr, const int32_t* __restrict__ sedge,
+                const double* __restrict__ scoef, const double* __restrict__ a_val, double* __restrict__ c_val,
+                const int64_t* __restrict__ csr2ell, double* __restrict__ e64, float* __restrict__ e32,
+                double* __restrict__ d64, float* __restrict__ d32, double* __restrict__ di64,
+                float* __restrict__ di32, int* __restrict__ err) {
+  const int64_t i1 = g1 * 32;
+  for (int64_t i = g0 * 32 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < i1;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = i >> 5, lane = i & 31;
+    const int64_t base = sptr[g] + lane, width = (sptr[g + 1] - sptr[g]) >> 5;
+    double acc = 0.0;
+    for (int64_t k0 = 0; k0 < width; k0 += B) {
+      int ed[B];
+      double cf[B], av[B];
+#pragma unroll
+      for (int j = 0; j < B; ++j)
+        if (k0 + j < width) {
+          ed[j] = sedge[base + (k0 + j) * 32];
+          cf[j] = scoef[base + (k0 + j) * 32];
         }
-      }
+#pragma unroll
+      for (int j = 0; j < B; ++j)
+        if (k0 + j < width) av[j] = a_val[ed[j]];
+#pragma unroll
+      for (int j = 0; j < B; ++j)
+        if (k0 + j < width) acc = __fma_rn(cf[j], av[j], acc);
     }
+    emit_entry(up_entry[i], mirror[i], acc, c_val, csr2ell, e64, e32, d64, d32, di64, di32, err);
   }
 }
 
@@ -434,94 +499,151 @@ __global__ void k_scatter_values(int64_t nnz, const int64_t* __restrict__ csr2el
 
 // Dense coarsest operator in the level's colour-permuted numbering (the
 // numbering of the vectors the cycle hands to the coarse solve).
-__global__ void k_csr_to_dense(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+__global__ void k_csr_to_dense(int64_t n, int64_t ld, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                const double* __restrict__ val, const int32_t* __restrict__ iperm,
                                double* __restrict__ D) {
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     const int64_t pi = iperm[i];
-    for (int64_t k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x) D[pi * n + iperm[col[k]]] = val[k];
+    for (int64_t k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x) D[pi * ld + iperm[col[k]]] = val[k];
   }
 }
 
-// ---- dense FP64 Cholesky, right-looking, 32 x 32 blocks ----
-// k_chol_panel factors the diagonal block p in every CTA's shared memory
-// (identical arithmetic in every CTA), CTA 0 stores the factor L_pp in Dbuf,
-// and every CTA solves its rows below the block: L_ip = A_ip L_pp^-T.
-// k_chol_update then applies the trailing update; k_chol_store_diag writes
-// the stored diagonal factors into A once all steps are done (block p of A is
-// not read again after step p).  status bit 0: a pivot <= 0.
-__device__ void chol_factor_block(double (&D)[32][33], double (&rdiag)[32], int nb, int* bad) {
-  for (int k = 0; k < nb; ++k) {
-    if (threadIdx.x == 0) {
-      double d = D[k][k];
+// ---- explicit inverse of the coarsest operator by block sweeps ----
+// The coarse solve applies A_lambda^-1 as a GEMV; the inverse is formed by
+// the symmetric sweep operator (Gauss-Jordan elimination without pivoting,
+// stable on SPD matrices), 32 x 32 blocks.  S is the operator padded to
+// npad = 32 nbk rows (identity on the padded diagonal), row-major with
+// leading dimension npad; only its lower triangle (S_ij, i >= j) is stored.
+// Sweeping pivot block P replaces
+//   S_PP by -S_PP^-1,   S_IP by S_IP S_PP^-1   (I != P),
+//   S_IJ by S_IJ - S_IP S_PP^-1 S_PJ          (I, J != P),
+// with S_PJ = S_JP^T; after every block has been swept S = -A^-1.  Each pivot
+// is a Schur complement of A, hence SPD when A is (status bit 0 otherwise).
+// One sweep is two launches: the panel (the pivot column before the sweep,
+// U = S_:P, and U S_PP^-1) and the update of every lower tile; the last CTA
+// to finish the next pivot tile inverts it for the following sweep.
+
+__device__ __forceinline__ double sym_at(const double* S, int ld, int i, int j) {
+  return i >= j ? S[(int64_t)i * ld + j] : S[(int64_t)j * ld + i];
+}
+
+// 1 / d by Newton-Raphson iteration r <- r (2 - d r), written as
+// e = 1 - d r, r <- r + r e, from the FP32 reciprocal (about 2^-23 relative
+// error; two steps reach the FP64 rounding level).  Values outside the FP32
+// range use the FP64 division.
+__device__ __forceinline__ double recip_newton(double d) {
+  const float f = (float)d;
+  if (!(fabsf(f) >= 1e-30f && fabsf(f) <= 1e30f)) return 1.0 / d;
+  double r = (double)__frcp_rn(f);
+  double e = __fma_rn(-d, r, 1.0);
+  r = __fma_rn(r, e, r);
+  e = __fma_rn(-d, r, 1.0);
+  return __fma_rn(r, e, r);
+}
+
+// m <- m^-1 for a 32 x 32 SPD block held in both triangles, by 32 scalar
+// sweeps of its lower triangle (528 entries over the 256 threads, so the FP64
+// work is spread over all four SM sub-partitions); warp 0 forms each step's
+// pivot reciprocal and scaled column.  A pivot that is not positive sets
+// *bad and is replaced by 1.  blockDim.x == 256; all threads must call it.
+__device__ void sweep_inverse32(double (&m)[32][33], int* bad) {
+  __shared__ double ck[32], cs[32], sdk;
+  const int tid = threadIdx.x;
+  int ei[3], ej[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int e = tid + 256 * q;
+    int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    while (i * (i + 1) / 2 > e) --i;
+    ei[q] = e < 528 ? i : -1;
+    ej[q] = e - i * (i + 1) / 2;
+  }
+  for (int k = 0; k < 32; ++k) {
+    if (tid < 32) {
+      double d = m[k][k];
       if (!(d > 0.0)) {
-        *bad = 1;
+        if (tid == 0) *bad = 1;
         d = 1.0;
       }
-      const double l = sqrt(d);
-      D[k][k] = l;
-      rdiag[k] = 1.0 / l;
+      const double dk = recip_newton(d);
+      const double c = tid >= k ? m[tid][k] : m[k][tid];
+      ck[tid] = c;
+      cs[tid] = c * dk;
+      if (tid == 0) sdk = dk;
     }
     __syncthreads();
-    for (int r = k + 1 + threadIdx.x; r < nb; r += blockDim.x) D[r][k] *= rdiag[k];
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-      const int r = idx >> 5, c = idx & 31;
-      if (c > k && r >= c && r < nb) D[r][c] -= D[r][k] * D[c][k];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int i = ei[q], j = ej[q];
+      if (i < 0) continue;
+      double v;
+      if (i == k && j == k)
+        v = -sdk;
+      else if (i == k)
+        v = cs[j];
+      else if (j == k)
+        v = cs[i];
+      else
+        v = m[i][j] - ck[i] * cs[j];
+      m[i][j] = v;
     }
     __syncthreads();
   }
-}
-
-__global__ void k_chol_panel(int n, int p, double* __restrict__ A, double* __restrict__ Dbuf,
-                             int* __restrict__ status) {
-  __shared__ double D[32][33];
-  __shared__ double rdiag[32];
-  __shared__ int bad;
-  const int j0 = p * 32;
-  const int nb = min(32, n - j0);
-  if (threadIdx.x == 0) bad = 0;
-  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-    const int r = idx >> 5, c = idx & 31;
-    D[r][c] = (r < nb && c < nb) ? A[(int64_t)(j0 + r) * n + j0 + c] : (r == c ? 1.0 : 0.0);
-  }
+  // the lower triangle holds -m^-1: negate, then mirror
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    if (ei[q] >= 0) m[ei[q]][ej[q]] = -m[ei[q]][ej[q]];
   __syncthreads();
-  chol_factor_block(D, rdiag, nb, &bad);
-  if (blockIdx.x == 0) {
-    if (bad && threadIdx.x == 0) atomicOr(status, 1);
-    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-      const int r = idx >> 5, c = idx & 31;
-      Dbuf[(int64_t)p * 1024 + idx] = (c <= r) ? D[r][c] : 0.0;
-    }
-  }
-  const int i = j0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    double v[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) v[c] = c < nb ? A[(int64_t)i * n + j0 + c] : 0.0;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      if (c < nb) {
-        double s = v[c];
-#pragma unroll
-        for (int k = 0; k < c; ++k) s -= v[k] * D[c][k];
-        v[c] = s * rdiag[c];
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < nb) A[(int64_t)i * n + j0 + c] = v[c];
+  for (int q = 0; q < 3; ++q)
+    if (ei[q] >= 0 && ei[q] != ej[q]) m[ej[q]][ei[q]] = m[ei[q]][ej[q]];
+  __syncthreads();
+}
+
+// S = 0 with ones on the padded diagonal (rows n .. npad-1).
+__global__ void k_gj_pad(int npad, int n, double* __restrict__ S) {
+  const int64_t total = (int64_t)npad * npad;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / npad, j = e % npad;
+    S[e] = (i == j && i >= n) ? 1.0 : 0.0;
   }
 }
 
-__global__ void k_chol_store_diag(int n, const double* __restrict__ Dbuf, double* __restrict__ A) {
-  const int p = blockIdx.x;
-  const int j0 = p * 32;
-  const int nb = min(32, n - j0);
-  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-    const int r = idx >> 5, c = idx & 31;
-    if (r < nb && c < nb) A[(int64_t)(j0 + r) * n + j0 + c] = Dbuf[(int64_t)p * 1024 + idx];
-  }
+// Dinv = S_00^-1 (the first pivot).
+__global__ void __launch_bounds__(256) k_gj_first(int npad, const double* __restrict__ S, double* __restrict__ Dinv,
+                                                  int* __restrict__ status) {
+  __shared__ double m[32][33];
+  __shared__ int bad;
+  pdl_wait();
+  pdl_trigger();
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < 1024; e += 256) m[e >> 5][e & 31] = sym_at(S, npad, e >> 5, e & 31);
+  __syncthreads();
+  sweep_inverse32(m, &bad);
+  for (int e = threadIdx.x; e < 1024; e += 256) Dinv[e] = m[e >> 5][e & 31];
+  if (threadIdx.x == 0 && bad) atomicOr(status, 1);
+}
+
+// Panel of sweep P, 8 rows per CTA: Uo[r][k] = S_{r, 32P+k} (before the
+// sweep), Uh[r][k] = sum_j Uo[r][j] Dinv[j][k].
+__global__ void __launch_bounds__(256) k_gj_panel(int npad, int P, const double* __restrict__ S,
+                                                  const double* __restrict__ Dinv, double* __restrict__ Uo,
+                                                  double* __restrict__ Uh) {
+  __shared__ double D[32][33], u[8][32];
+  pdl_wait();
+  pdl_trigger();
+  const int tid = threadIdx.x, rr = tid >> 5, k = tid & 31;
+  const int r = blockIdx.x * 8 + rr;
+  for (int e = tid; e < 1024; e += 256) D[e >> 5][e & 31] = Dinv[e];
+  const double v = sym_at(S, npad, r, P * 32 + k);
+  u[rr][k] = v;
+  Uo[(int64_t)r * 32 + k] = v;
+  __syncthreads();
+  double acc = 0.0;
+#pragma unroll 8
+  for (int j = 0; j < 32; ++j) acc += u[rr][j] * D[j][k];
+  Uh[(int64_t)r * 32 + k] = acc;
 }
 
 // Maps a linear tile index to (I, J), J in [first, nbk), I in [J, nbk).
@@ -535,94 +657,78 @@ __device__ __forceinline__ void lower_tile(int t, int first, int nbk, int* I, in
   *I = j + t;
 }
 
-// Trailing update A_IJ -= L_Ip L_Jp^T for the lower tiles right of block p.
-__global__ void k_chol_update(int n, int p, double* __restrict__ A) {
-  __shared__ double Li[32][33], Lj[32][33];
-  const int nbk = (n + 31) / 32;
+// Update of sweep P, one CTA per 8-row quarter of a lower tile.  The four
+// quarters of the next pivot tile (P+1, P+1) come first; the last of them to
+// finish (arrival counter cnt[P]) inverts that tile into DinvNext.
+__global__ void __launch_bounds__(256) k_gj_update(int npad, int P, double* __restrict__ S,
+                                                   const double* __restrict__ Dinv, const double* __restrict__ Uo,
+                                                   const double* __restrict__ Uh, int* __restrict__ cnt,
+                                                   double* __restrict__ DinvNext, int* __restrict__ status) {
+  __shared__ double uo[32][33], uh[8][33];
+  __shared__ double m[32][33];
+  __shared__ int last, bad;
+  pdl_wait();
+  pdl_trigger();
+  const int nbk = npad / 32;
+  const int tid = threadIdx.x, rr = tid >> 5, cc = tid & 31;
+  const int q = blockIdx.x & 3, tt = blockIdx.x >> 2;
+  const bool has_next = P + 1 < nbk;
+  int t = tt;
+  if (has_next) {  // move the next pivot tile to the front of the order
+    const int tD = (P + 1) * nbk - P * (P + 1) / 2;  // lower_tile index of (P+1, P+1)
+    t = tt == 0 ? tD : (tt <= tD ? tt - 1 : tt);
+  }
   int I, J;
-  lower_tile(blockIdx.x, p + 1, nbk, &I, &J);
-  const int j0 = p * 32;
-  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-    const int r = idx >> 5, k = idx & 31;
-    const int gi = I * 32 + r, gj = J * 32 + r, gk = j0 + k;
-    Li[r][k] = (gi < n && gk < n) ? A[(int64_t)gi * n + gk] : 0.0;
-    Lj[r][k] = (gj < n && gk < n) ? A[(int64_t)gj * n + gk] : 0.0;
+  lower_tile(t, 0, nbk, &I, &J);
+  const int r = I * 32 + q * 8 + rr, c = J * 32 + cc;
+  double* out = S + (int64_t)r * npad + c;
+  if (I == P && J == P) {
+    *out = -Dinv[(r - P * 32) * 32 + cc];
+  } else if (J == P) {
+    *out = Uh[(int64_t)r * 32 + cc];
+  } else if (I == P) {
+    *out = Uh[(int64_t)c * 32 + (r - P * 32)];
+  } else {
+    for (int e = tid; e < 1024; e += 256) uo[e >> 5][e & 31] = Uo[(int64_t)(J * 32 + (e >> 5)) * 32 + (e & 31)];
+    uh[rr][cc] = Uh[(int64_t)r * 32 + cc];
+    __syncthreads();
+    double acc = 0.0;
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) acc += uh[rr][k] * uo[cc][k];
+    *out -= acc;
+  }
+  if (!has_next || I != P + 1 || J != P + 1) return;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    last = atomicAdd(cnt + P, 1) == 3;
+    bad = 0;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-    const int r = idx >> 5, c = idx & 31;
-    const int gi = I * 32 + r, gj = J * 32 + c;
-    if (gi < n && gj < n && gj <= gi) {
-      double s = 0.0;
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) s += Li[r][k] * Lj[c][k];
-      A[(int64_t)gi * n + gj] -= s;
-    }
+  if (!last) return;
+  __threadfence();
+  const double* T = S + (int64_t)(P + 1) * 32 * npad + (P + 1) * 32;
+  for (int e = tid; e < 1024; e += 256) {
+    const int i = e >> 5, j = e & 31;
+    m[i][j] = __ldcg(T + (int64_t)(i >= j ? i : j) * npad + (i >= j ? j : i));
   }
+  __syncthreads();
+  sweep_inverse32(m, &bad);
+  for (int e = tid; e < 1024; e += 256) DinvNext[e] = m[e >> 5][e & 31];
+  if (tid == 0 && bad) atomicOr(status, 1);
 }
 
-// rdiag[i] = 1 / L_ii
-__global__ void k_recip_diag(int n, const double* __restrict__ Lf, double* __restrict__ rdiag) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    rdiag[i] = 1.0 / Lf[(int64_t)i * n + i];
-}
-
-// Wt = (L^-1)^T: row k of Wt is column k of L^-1, by forward substitution
-// (one warp per column; Wt must be zero-initialised).
-__global__ void k_tri_inverse(int n, const double* __restrict__ Lf, const double* __restrict__ rdiag,
-                              double* __restrict__ Wt) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  const int k = warp;
-  double* w = Wt + (int64_t)k * n;
-  if (lane == 0) w[k] = rdiag[k];
-  __syncwarp();
-  for (int i = k + 1; i < n; ++i) {
-    const double* Li = Lf + (int64_t)i * n;
-    double s = 0.0;
-    for (int m = k + lane; m < i; m += 32) s += Li[m] * w[m];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) w[i] = -s * rdiag[i];
-    __syncwarp();
-  }
-}
-
-// Ainv = L^-T L^-1: Ainv_ij = sum_k Wt[i][k] Wt[j][k]; lower tiles computed,
-// both halves written.
-__global__ void k_inv_gram(int n, const double* __restrict__ Wt, double* __restrict__ Ainv) {
-  __shared__ double Ti[32][33], Tj[32][33];
-  const int nbk = (n + 31) / 32;
-  int I, J;
-  lower_tile(blockIdx.x, 0, nbk, &I, &J);
-  double acc[4] = {0, 0, 0, 0};
-  for (int kb = I; kb < nbk; ++kb) {  // Wt[i][k] = 0 for k < i
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-      const int r = idx >> 5, k = idx & 31;
-      const int gi = I * 32 + r, gj = J * 32 + r, gk = kb * 32 + k;
-      Ti[r][k] = (gi < n && gk < n) ? Wt[(int64_t)gi * n + gk] : 0.0;
-      Tj[r][k] = (gj < n && gk < n) ? Wt[(int64_t)gj * n + gk] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int idx = threadIdx.x + q * 256;
-      const int r = idx >> 5, c = idx & 31;
-      double s = 0.0;
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) s += Ti[r][k] * Tj[c][k];
-      acc[q] += s;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int idx = threadIdx.x + q * 256;
-    const int r = idx >> 5, c = idx & 31;
-    const int gi = I * 32 + r, gj = J * 32 + c;
-    if (gi < n && gj < n) {
-      Ainv[(int64_t)gi * n + gj] = acc[q];
-      Ainv[(int64_t)gj * n + gi] = acc[q];
-    }
+// Ainv = -S (both triangles, leading dimension n), and its FP32 copy.
+__global__ void k_gj_finish(int n, int npad, const double* __restrict__ S, double* __restrict__ Ainv,
+                            float* __restrict__ Ainv32) {
+  pdl_wait();
+  pdl_trigger();
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const double v = -sym_at(S, npad, i, j);
+    Ainv[e] = v;
+    Ainv32[e] = (float)v;
   }
 }
 
@@ -914,7 +1020,65 @@ static gmg_status galerkin_symbolic(gmg_ctx* c, int l, cudaStream_t s, std::vect
                                                    F.p_idx_o, F.p_w_o, C.csr_rowptr, C.csr_col, C.plan_ptr,
                                                    C.plan_edge, C.plan_coef);
   GMG_LAUNCHED();
+  // sliced layout of the plan (entries with terms, sorted by term count)
+  std::vector<int64_t> hp(C.nnz + 1);
+  GMG_CK(cudaMemcpyAsync(hp.data(), C.plan_ptr, (C.nnz + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   GMG_CK(cudaStreamSynchronize(s));
+  std::vector<int32_t> up;
+  for (int64_t e = 0; e < C.nnz; ++e)
+    if (hp[e + 1] > hp[e]) up.push_back((int32_t)e);
+  std::stable_sort(up.begin(), up.end(), [&](int32_t a, int32_t b) { return hp[a + 1] - hp[a] > hp[b + 1] - hp[b]; });
+  const int64_t nup = (int64_t)up.size();
+  if (nup == 0) {
+    set_error("Galerkin level " + std::to_string(l + 1) + ": empty product");
+    return GMG_ERR_INVALID_ARG;
+  }
+  const int64_t nsl = (nup + 31) / 32;
+  std::vector<int64_t> sptr(nsl + 1, 0);
+  C.plan_long_slices = 0;
+  for (int64_t g = 0; g < nsl; ++g) {
+    const int64_t width = hp[up[32 * g] + 1] - hp[up[32 * g]];
+    sptr[g + 1] = sptr[g] + 32 * width;
+    if (width > kGalLongWidth) C.plan_long_slices = g + 1;  // widths are non-increasing
+  }
+  while ((int64_t)up.size() < 32 * nsl) up.push_back(up.back());  // pad the last slice with a repeated entry
+  C.plan_nup = 32 * nsl;
+  // CSR position of every entry's mirror (K, J), -1 on the diagonal
+  std::vector<int32_t> row_of(C.nnz);
+  for (int64_t J = 0; J < nc; ++J)
+    for (int64_t e = hrp[J]; e < hrp[J + 1]; ++e) row_of[e] = (int32_t)J;
+  std::vector<int32_t> mir(up.size());
+  for (size_t i = 0; i < up.size(); ++i) {
+    const int32_t J = row_of[up[i]], K = hcol[up[i]];
+    if (K == J) {
+      mir[i] = -1;
+      continue;
+    }
+    const int32_t* b0 = hcol.data() + hrp[K];
+    const int32_t* b1 = hcol.data() + hrp[K + 1];
+    const int32_t* f = std::lower_bound(b0, b1, J);
+    if (f == b1 || *f != J) {
+      set_error("Galerkin level " + std::to_string(l + 1) + ": pattern not symmetric");
+      return GMG_ERR_INVALID_ARG;
+    }
+    mir[i] = (int32_t)(f - hcol.data());
+  }
+  GMG_TRY(upload(c->arena, &C.plan_mirror, mir.data(), mir.size()));
+  GMG_TRY(upload(c->arena, &C.plan_up, up.data(), up.size()));
+  GMG_TRY(upload(c->arena, &C.plan_sptr, sptr.data(), sptr.size()));
+  GMG_TRY(c->arena.alloc(&C.plan_sedge, (size_t)sptr.back()));
+  GMG_TRY(c->arena.alloc(&C.plan_scoef, (size_t)sptr.back()));
+  k_plan_slice<<<grid_for(C.plan_nup, 256), 256, 0, s>>>(C.plan_nup, C.plan_up, C.plan_ptr, C.plan_edge, C.plan_coef,
+                                                          C.plan_sptr, C.plan_sedge, C.plan_scoef);
+  GMG_LAUNCHED();
+  GMG_CK(cudaStreamSynchronize(s));
+  c->arena.release_one(C.plan_edge);
+  c->arena.release_one(C.plan_coef);
+  c->arena.release_one(C.plan_ptr);
+  c->arena.release_one(terms);
+  C.plan_edge = nullptr;
+  C.plan_coef = nullptr;
+  C.plan_ptr = nullptr;
   return GMG_OK;
 }
 
@@ -926,42 +1090,47 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s) {
     Level& F = c->L[l];
     if (l > 0) {
       Level& P = c->L[l - 1];
-      k_gal_apply<<<grid_for(F.nnz, 256), 256, 0, s>>>(F.nnz, F.plan_ptr, F.plan_edge, F.plan_coef, P.csr_val,
-                                                      F.csr_val);
-      GMG_LAUNCHED();
-      k_gal_mirror<<<grid_for(F.n, 256), 256, 0, s>>>(F.n, F.csr_rowptr, F.csr_col, F.csr_val);
+      const int64_t nsl = F.plan_nup / 32, nlong = F.plan_long_slices;
+      if (nlong > 0) {
+        k_gal_level<32><<<grid_for(nlong * 32, kGalThreads, 152 * 128), kGalThreads, 0, s>>>(
+            0, nlong, F.plan_up, F.plan_mirror, F.plan_sptr, F.plan_sedge, F.plan_scoef, P.csr_val, F.csr_val,
+            F.csr2ell, F.A.v64, F.A.v32, F.diag64, F.diag32, F.dinv64, F.dinv32, c->dstatus);
+        GMG_LAUNCHED();
+      }
+      if (nsl > nlong) {
+        k_gal_level<8><<<grid_for((nsl - nlong) * 32, kGalThreads, 152 * 128), kGalThreads, 0, s>>>(
+            nlong, nsl, F.plan_up, F.plan_mirror, F.plan_sptr, F.plan_sedge, F.plan_scoef, P.csr_val, F.csr_val,
+            F.csr2ell, F.A.v64, F.A.v32, F.diag64, F.diag32, F.dinv64, F.dinv32, c->dstatus);
+        GMG_LAUNCHED();
+      }
+    } else {
+      k_scatter_values<<<grid_for(F.nnz, 256), 256, 0, s>>>(F.nnz, F.csr2ell, F.csr_val, F.A.v64, F.A.v32,
+                                                           F.diag64, F.diag32, F.dinv64, F.dinv32, c->dstatus);
       GMG_LAUNCHED();
     }
-    k_scatter_values<<<grid_for(F.nnz, 256), 256, 0, s>>>(F.nnz, F.csr2ell, F.csr_val, F.A.v64, F.A.v32, F.diag64,
-                                                         F.diag32, F.dinv64, F.dinv32, c->dstatus);
-    GMG_LAUNCHED();
   }
-  // coarsest: dense Cholesky and explicit inverse
+  // coarsest: explicit inverse by block sweeps
   Level& C = c->L[c->nlev - 1];
   const int n = (int)c->nco;
-  GMG_CK(cudaMemsetAsync(c->dense, 0, sizeof(double) * (size_t)n * n, s));
-  k_csr_to_dense<<<std::min(n, 4096), 128, 0, s>>>(n, C.csr_rowptr, C.csr_col, C.csr_val, C.iperm, c->dense);
+  const int nbk = (n + 31) / 32, npad = nbk * 32;
+  double* Dinv[2] = {c->dbuf, c->dbuf + 1024};
+  double* Uo = c->dbuf + 2048;
+  double* Uh = Uo + (size_t)npad * 32;
+  GMG_CK(cudaMemsetAsync(c->gj_cnt, 0, sizeof(int) * (size_t)nbk, s));
+  k_gj_pad<<<grid_for((int64_t)npad * npad, 256), 256, 0, s>>>(npad, n, c->dense);
   GMG_LAUNCHED();
-  const int nbk = (n + 31) / 32;
+  k_csr_to_dense<<<std::min(n, 4096), 128, 0, s>>>(n, npad, C.csr_rowptr, C.csr_col, C.csr_val, C.iperm, c->dense);
+  GMG_LAUNCHED();
+  GMG_TRY(launch(k_gj_first, 1, 256, s, npad, (const double*)c->dense, Dinv[0], c->dstatus + 1));
   for (int p = 0; p < nbk; ++p) {
-    const int below = n - std::min(n, (p + 1) * 32);
-    k_chol_panel<<<std::max(1, (below + 127) / 128), 128, 0, s>>>(n, p, c->dense, c->dbuf, c->dstatus + 1);
-    GMG_LAUNCHED();
-    const int T = nbk - p - 1;
-    if (T > 0) {
-      k_chol_update<<<T * (T + 1) / 2, 256, 0, s>>>(n, p, c->dense);
-      GMG_LAUNCHED();
-    }
+    GMG_TRY(launch(k_gj_panel, npad / 8, 256, s, npad, p, (const double*)c->dense, (const double*)Dinv[p & 1], Uo,
+                   Uh));
+    GMG_TRY(launch(k_gj_update, (int64_t)4 * nbk * (nbk + 1) / 2, 256, s, npad, p, c->dense,
+                   (const double*)Dinv[p & 1], (const double*)Uo, (const double*)Uh, c->gj_cnt, Dinv[(p + 1) & 1],
+                   c->dstatus + 1));
   }
-  k_chol_store_diag<<<nbk, 256, 0, s>>>(n, c->dbuf, c->dense);
-  GMG_LAUNCHED();
-  k_recip_diag<<<(n + 255) / 256, 256, 0, s>>>(n, c->dense, c->dbuf);
-  GMG_LAUNCHED();
-  GMG_CK(cudaMemsetAsync(c->Winv, 0, sizeof(double) * (size_t)n * n, s));
-  k_tri_inverse<<<(n + 3) / 4, 128, 0, s>>>(n, c->dense, c->dbuf, c->Winv);
-  GMG_LAUNCHED();
-  k_inv_gram<<<nbk * (nbk + 1) / 2, 256, 0, s>>>(n, c->Winv, c->Ainv);
-  GMG_LAUNCHED();
+  GMG_TRY(launch(k_gj_finish, grid_for((int64_t)n * n, 256), 256, s, n, npad, (const double*)c->dense, c->Ainv,
+                 c->Ainv32));
   int h[2] = {0, 0};
   GMG_CK(cudaMemcpyAsync(h, c->dstatus, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   GMG_CK(cudaStreamSynchronize(s));
@@ -974,7 +1143,7 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s) {
     return GMG_ERR_NOT_SPD;
   }
   if (h[1]) {
-    set_error("Cholesky pivot <= 0 on the coarsest level");
+    set_error("coarsest operator not positive definite (sweep pivot <= 0)");
     return GMG_ERR_CHOLESKY;
   }
   c->values_ready = true;
@@ -1081,55 +1250,108 @@ static gmg_status validate(const gmg_csr* A, int nP, const gmg_prolong* P) {
   return GMG_OK;
 }
 
-// Descriptors of every level for the persistent small-level kernel; the
-// first level with at most kClusterMaxRows rows (below the finest) starts it.
-static gmg_status build_small_level_descriptors(gmg_ctx* c) {
-  // Off by default: measured on GB300 (1M-vertex torus) a cluster phase costs
-  // 3-4 us against about 2 us for a PDL-chained launch.  GMG_CLUSTER_L0=l
-  // starts the cluster kernel at level l.
-  c->cluster_l0 = 0;
-  if (const char* e = std::getenv("GMG_CLUSTER_L0")) c->cluster_l0 = std::atoi(e);
-  if (c->cluster_l0 < 0 || c->cluster_l0 >= c->nlev) c->cluster_l0 = 0;
-  std::vector<DevLevel> d(c->nlev);
-  for (int l = 0; l < c->nlev; ++l) {
-    Level& L = c->L[l];
-    DevLevel& v = d[l];
-    std::memset(&v, 0, sizeof(v));
-    v.n = L.n;
-    v.ncolor = L.ncolor;
-    v.lanes = L.lanes;
-    int64_t* cso;
-    GMG_TRY(upload(c->arena, &cso, L.color_slice_off.data(), L.color_slice_off.size()));
-    v.cso = cso;
-    v.nslice = L.A.nslice;
-    v.a_ptr = L.A.ptr;
-    v.a_row0 = L.A.row0;
-    v.a_nrow = L.A.nrow;
-    v.a_col = L.A.col;
-    v.a_v32 = L.A.v32;
-    v.a_v64 = L.A.v64;
-    v.dinv32 = L.dinv32;
-    v.diag32 = L.diag32;
-    v.dinv64 = L.dinv64;
-    v.diag64 = L.diag64;
-    v.r_nslice = L.R.nslice;
-    v.r_ptr = L.R.ptr;
-    v.r_row0 = L.R.row0;
-    v.r_nrow = L.R.nrow;
-    v.r_col = L.R.col;
-    v.r_v32 = L.R.v32;
-    v.r_v64 = L.R.v64;
-    v.p_idx = L.p_idx;
-    v.p_w32 = L.p_w32;
-    v.p_w64 = L.p_w64;
-    v.x32 = L.x32;
-    v.b32 = L.b32;
-    v.r32 = L.r32;
-    v.x64 = L.x64;
-    v.b64 = L.b64;
-    v.r64 = L.r64;
+// Tail of the FP32 cycle: the smoothed levels l0 .. lambda-1 (at most
+// kMaxTail, l0 >= 1) and the coarsest level run as one cluster launch when
+// their shared-memory copies fit in kTailSmemLimit bytes per CTA; l0 is the
+// smallest level index that fits.  16 CTAs per cluster if the device can
+// schedule them, else 8; off if neither fits or GMG_NO_TAIL=1.
+static gmg_status build_tail(gmg_ctx* c) {
+  c->tail_l0 = 0;
+  const int lam = c->nlev - 1;
+  if (const char* e = std::getenv("GMG_NO_TAIL"))
+    if (e[0] == '1') return GMG_OK;
+  if (lam < 2) return GMG_OK;
+  auto al = [](int64_t v) { return (v + 15) & ~(int64_t)15; };
+  // slice widths of every level (host)
+  std::vector<std::vector<int64_t>> ptr(c->nlev);
+  for (int l = std::max(1, lam - kMaxTail); l < lam; ++l) {
+    ptr[l].resize(c->L[l].A.nslice + 1);
+    GMG_CK(cudaMemcpy(ptr[l].data(), c->L[l].A.ptr, ptr[l].size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
   }
-  return upload(c->arena, &c->dlv, d.data(), d.size());
+  for (int ncta : {16, 8}) {
+    for (int l0 = std::max(1, lam - kMaxTail); l0 < lam; ++l0) {
+      TailDesc D{};
+      std::vector<std::vector<int32_t>> soff(lam);
+      int64_t cur = 0;
+      for (int l = l0; l < lam; ++l) {
+        Level& L = c->L[l];
+        TailLevel& T = D.lv[l - l0];
+        const int64_t ns = L.A.nslice;
+        soff[l].assign(ns, 0);
+        int64_t emax = 0;
+        for (int cta = 0; cta < ncta; ++cta) {
+          int64_t off = 0;
+          for (int k = 0; k < L.ncolor; ++k)
+            for (int64_t sl = L.color_slice_off[k] + cta; sl < L.color_slice_off[k + 1]; sl += ncta) {
+              soff[l][sl] = (int32_t)off;
+              off += ptr[l][sl + 1] - ptr[l][sl];
+            }
+          emax = std::max(emax, off);
+        }
+        T.n = (int)L.n;
+        T.ncolor = L.ncolor;
+        T.nslice = (int)ns;
+        T.r_nslice = (int)L.R.nslice;
+        T.o_x = (int)cur; cur = al(cur + 4 * L.n);
+        T.o_r = (int)cur; cur = al(cur + 4 * L.n);
+        T.o_b = (int)cur; cur = al(cur + 4 * L.n);
+        T.o_dinv = (int)cur; cur = al(cur + 4 * L.n);
+        T.o_diag = (int)cur; cur = al(cur + 4 * L.n);
+        T.o_row0 = (int)cur; cur = al(cur + 4 * ns);
+        T.o_nrow = (int)cur; cur = al(cur + 4 * ns);
+        T.o_width = (int)cur; cur = al(cur + 4 * ns);
+        T.o_soff = (int)cur; cur = al(cur + 4 * ns);
+        T.o_cso = (int)cur; cur = al(cur + 4 * (L.ncolor + 1));
+        T.o_val = (int)cur; cur = al(cur + 4 * emax);
+        T.o_col = (int)cur; cur = al(cur + 4 * emax);
+      }
+      D.nc = (int)c->L[lam].n;
+      D.o_xc = (int)cur; cur = al(cur + 4 * D.nc);
+      D.o_bc = (int)cur; cur = al(cur + 4 * D.nc);
+      if (cur > kTailSmemLimit) continue;
+      bool ok = false;
+      GMG_TRY(tail_configure(c, ncta, (int)cur, &ok));
+      if (!ok) break;  // this cluster size cannot be scheduled: try the next
+      // fill the global pointers and upload the per-slice tables
+      for (int l = l0; l < lam; ++l) {
+        Level& L = c->L[l];
+        TailLevel& T = D.lv[l - l0];
+        int32_t *so, *cs;
+        GMG_TRY(upload(c->arena, &so, soff[l].data(), soff[l].size()));
+        std::vector<int32_t> cso32(L.color_slice_off.begin(), L.color_slice_off.end());
+        GMG_TRY(upload(c->arena, &cs, cso32.data(), cso32.size()));
+        T.soff = so;
+        T.cso = cs;
+        T.a_ptr = L.A.ptr;
+        T.a_row0 = L.A.row0;
+        T.a_nrow = L.A.nrow;
+        T.a_col = L.A.col;
+        T.a_v32 = L.A.v32;
+        T.dinv32 = L.dinv32;
+        T.diag32 = L.diag32;
+        T.r_ptr = L.R.ptr;
+        T.r_row0 = L.R.row0;
+        T.r_nrow = L.R.nrow;
+        T.r_col = L.R.col;
+        T.r_v32 = L.R.v32;
+        T.p_idx = L.p_idx;
+        T.p_w32 = L.p_w32;
+        T.x32 = L.x32;
+        T.b32 = L.b32;
+      }
+      D.ntail = lam - l0;
+      D.ncta = ncta;
+      D.nu_pre = c->opt.nu_pre;
+      D.nu_post = c->opt.nu_post;
+      D.post_forward = c->opt.post_forward;
+      D.ainv32 = c->Ainv32;
+      c->tail = D;
+      c->tail_smem = (int)cur;
+      c->tail_l0 = l0;
+      return GMG_OK;
+    }
+  }
+  return GMG_OK;
 }
 
 gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P, cudaStream_t s) {
@@ -1187,10 +1409,14 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
     GMG_TRY(build_transfer_structure(c, l, P[l], perm[l], iperm[l], perm[l + 1], iperm[l + 1]));
   // coarsest dense buffers
   c->nco = c->L[c->nlev - 1].n;
-  GMG_TRY(a.alloc(&c->dense, (size_t)(c->nco * c->nco)));
-  GMG_TRY(a.alloc(&c->Winv, (size_t)(c->nco * c->nco)));
-  GMG_TRY(a.alloc(&c->Ainv, (size_t)(c->nco * c->nco)));
-  GMG_TRY(a.alloc(&c->dbuf, (size_t)(((c->nco + 31) / 32) * 1024 + c->nco)));
+  {
+    const int64_t nbk = (c->nco + 31) / 32, npad = 32 * nbk;
+    GMG_TRY(a.alloc(&c->dense, (size_t)(npad * npad)));
+    GMG_TRY(a.alloc(&c->Ainv, (size_t)(c->nco * c->nco)));
+    GMG_TRY(a.alloc(&c->Ainv32, (size_t)(c->nco * c->nco)));
+    GMG_TRY(a.alloc(&c->dbuf, (size_t)(2048 + 64 * npad)));  // two pivot inverses, panel U and U D^-1
+    GMG_TRY(a.alloc(&c->gj_cnt, (size_t)nbk));
+  }
   // outer-iteration vectors
   const int64_t n = L0.n;
   c->xs = L0.x64;  // the FP64 cycle runs directly on the outer iterate
@@ -1202,10 +1428,15 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   GMG_TRY(a.alloc(&c->ros, n));
   GMG_TRY(a.alloc(&c->io, n));
   GMG_TRY(a.alloc(&c->io2, n));
-  GMG_TRY(a.alloc(&c->red, (size_t)std::max<int64_t>(4 * kRedBlocks, L0.A.nslice / 8 + 64)));
+  // one partial per residual block: with rows split over G warps a block covers 8 / G slices,
+  // so up to one block per slice (G = 8)
+  c->red_cap = std::max<int64_t>(4 * kRedBlocks, L0.A.nslice + 64);
+  GMG_TRY(a.alloc(&c->red, (size_t)c->red_cap));
   GMG_TRY(a.alloc(&c->scal, 64));
+  GMG_TRY(a.alloc(&c->dloop, 2));
+  GMG_TRY(a.alloc(&c->dhist, (size_t)c->opt.max_iter + 2));
   GMG_CK(cudaMallocHost((void**)&c->h_scal, 64 * sizeof(double)));
-  GMG_TRY(build_small_level_descriptors(c));
+  GMG_TRY(build_tail(c));
   return numeric_setup(c, s);
 }
 

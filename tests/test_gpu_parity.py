@@ -231,3 +231,124 @@ def test_full_size_torus(gmg):
     x, it, rr, _, _ = g.solve(_t(s.b), tol=1e-10)
     assert np.linalg.norm(s.b - s.A @ _np(x)) / np.linalg.norm(s.b) <= 1e-10
     g.close()
+
+
+@pytest.mark.parametrize("split", [1, 2, 4, 8])
+def test_fixed_warp_split_matches(gmg, split):
+    """Every warps-per-row split of the smoothing sweeps gives the oracle's
+    V-cycle (only the summation order of a row changes); an unsupported split
+    is rejected and changes nothing."""
+    s = gi.torus_system(256, 120, 1e-4, 7)
+    o = oracle.Oracle(s.A, s.Ps)
+    g = gmg.Solver(s.A, s.Ps)
+    rng = np.random.default_rng(SEED + 5)
+    x0 = rng.standard_normal(s.n)
+    g.set_lanes([split] * (g.nlev - 1))
+    xo = o.vcycle(x0, s.b)
+    assert rel(_np(g.vcycle(_t(x0), _t(s.b), fp32=False)), xo) <= 1e-12
+    assert rel(_np(g.vcycle(_t(x0), _t(s.b), fp32=True)), xo) <= 1e-6
+    with pytest.raises(gmg.GMGError):
+        g.set_lanes([3] * (g.nlev - 1))
+    x, _, _, _, _ = g.solve(_t(s.b), tol=1e-10)
+    assert np.linalg.norm(s.b - s.A @ _np(x)) <= 1e-10 * np.linalg.norm(s.b)
+    g.close()
+
+
+def _dense_spd(n, seed, shift=1.0):
+    """Symmetric matrix B B^T / n + shift I stored as a full CSR pattern."""
+    import scipy.sparse as sp
+
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((n, n))
+    A = sp.csr_matrix(B @ B.T / n + shift * np.eye(n))
+    A.sort_indices()
+    return A
+
+
+@pytest.mark.parametrize("n", [1, 7, 32, 33, 96, 130, 511])
+def test_coarsest_inverse_sizes(gmg, n):
+    """Single-level hierarchies are the coarsest direct solve alone: padded
+    sizes (n not a multiple of the 32-row sweep block, one block, several)
+    against a dense LU solve."""
+    A = _dense_spd(n, 100 + n)
+    g = gmg.Solver(A, [])
+    rng = np.random.default_rng(n)
+    b = rng.standard_normal(n)
+    x, it, rr, _, st = g.solve(_t(b), tol=1e-10)
+    assert st == 0 and it == 1
+    xe = np.linalg.solve(A.toarray(), b)
+    assert rel(_np(x), xe) <= 1e-12 * max(1.0, np.linalg.cond(A.toarray()) / 100)
+    g.close()
+
+
+def test_coarsest_not_positive_definite_is_reported(gmg):
+    """A symmetric coarsest operator with a negative eigenvalue but a positive
+    diagonal passes the diagonal check and must be rejected by the pivot check
+    of the coarsest inverse."""
+    import scipy.sparse as sp
+
+    n = 40
+    A = sp.lil_matrix((n, n))
+    for i in range(n):
+        A[i, i] = 1.0
+    A[3, 4] = A[4, 3] = 2.0  # the 2 x 2 block [[1, 2], [2, 1]] has eigenvalue -1
+    A = A.tocsr()
+    A.sort_indices()
+    with pytest.raises(gmg.GMGError) as e:
+        gmg.Solver(A, [])
+    assert e.value.status == gmg.GMG_ERR_CHOLESKY
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_device_loop_matches_host_loop(gmg, precision):
+    """The outer iterations run in a device-side graph loop (conditional WHILE
+    node) unless per-cycle timing is on, which uses the host-driven loop: both
+    give the same iterate, iteration count and residual history, bit for bit,
+    including a run stopped by max_iter."""
+    s = gi.torus_system(256, 120, 1e-4, 7)
+    for max_iter, tol in ((100, 1e-10), (3, 1e-30)):
+        g = gmg.Solver(s.A, s.Ps, precision=precision, max_iter=max_iter)
+        runs = []
+        for prof in (False, True):
+            g.profile(prof)
+            x, it, rr, hist, st = g.solve(_t(s.b), tol=tol, history=max_iter + 1, raise_on_fail=False)
+            runs.append((_np(x), it, rr, np.array(hist), st))
+        (x0, it0, rr0, h0, st0), (x1, it1, rr1, h1, st1) = runs
+        assert (it0, st0) == (it1, st1)
+        assert np.array_equal(x0, x1) and rr0 == rr1
+        assert np.array_equal(h0[: it0 + 1], h1[: it1 + 1])
+        if max_iter == 3:
+            assert it0 == 3 and st0 == gmg.GMG_ERR_NOT_CONVERGED
+        else:
+            assert st0 == 0
+        g.close()
+
+
+def test_tail_cluster_matches_kernel_per_phase_path(gmg, monkeypatch):
+    """The FP32 cycle runs its last levels as one thread-block-cluster launch
+    (shared-memory copies, distributed shared-memory stores, cluster
+    barriers).  With it switched off (GMG_NO_TAIL=1) every phase is its own
+    kernel.  Both cycles match the oracle at the FP32 tolerance, and the
+    cluster form launches fewer kernels."""
+    s = gi.torus_system(256, 120, 1e-4, 7)
+    o = oracle.Oracle(s.A, s.Ps)
+    rng = np.random.default_rng(SEED + 9)
+    x0 = rng.standard_normal(s.n)
+    xo = o.vcycle(x0, s.b)
+    res = {}
+    for tail in (True, False):
+        if tail:
+            monkeypatch.delenv("GMG_NO_TAIL", raising=False)
+        else:
+            monkeypatch.setenv("GMG_NO_TAIL", "1")
+        g = gmg.Solver(s.A, s.Ps, precision=gmg.GMG_FP32_PCG)
+        assert g.nlev >= 3
+        k0 = gmg.kernel_launches()
+        xg = _np(g.vcycle(_t(x0), _t(s.b), fp32=True))
+        res[tail] = (xg, gmg.kernel_launches() - k0)
+        assert rel(xg, xo) <= 1e-6
+        x, it, rr, _, st = g.solve(_t(s.b), tol=1e-10)
+        assert st == 0 and np.linalg.norm(s.b - s.A @ _np(x)) <= 1e-10 * np.linalg.norm(s.b)
+        g.close()
+    assert res[True][1] < res[False][1]
+    assert rel(res[True][0], res[False][0]) <= 1e-6
