@@ -99,3 +99,19 @@ def knn_laplacian(P: np.ndarray, E: np.ndarray, h: float) -> sp.csr_matrix:
 def system_matrix(Mdiag: np.ndarray, L: sp.csr_matrix, t: float) -> sp.csr_matrix:
     """A = M + t L (M diagonal), CSR with sorted columns and explicit diagonal."""
     return _csr_sorted(sp.diags(Mdiag) + t * L)
+
+
+def poisson_matrix(Mdiag: np.ndarray, L: sp.csr_matrix, eta: float) -> sp.csr_matrix:
+    """A = S + eta M of Eq. (Poisson) (S = L here, M diagonal), CSR with sorted
+    columns and explicit diagonal."""
+    return _csr_sorted(L + sp.diags(eta * Mdiag))
+
+
+def bilaplacian_matrix(Mdiag: np.ndarray, L: sp.csr_matrix, alpha: float, beta: float) -> sp.csr_matrix:
+    """A = M + alpha S + beta S M^-1 S: the normal equations of the smoothing
+    energy (x - y)^T M (x - y) + alpha x^T S x + beta x^T S M^-1 S x of Sec. 5.5."""
+    SMS = L @ sp.diags(1.0 / Mdiag) @ L
+    B = sp.diags(Mdiag) + alpha * L + beta * SMS
+    # the sparse product rounds (i, j) and (j, i) in different orders: average
+    # the two halves so the matrix is exactly symmetric
+    return _csr_sorted(0.5 * (B + B.T))

@@ -13,6 +13,12 @@ prolongation hierarchy of Sec. 4 built on the surface's points and edges.
   heat512k    : jittered torus 1024 x 512 (524,288 vertices), t = 1e-3, u0 one-hot
                 at 16 random vertices, x_target ~ N(0, 1), seed 4
 
+Two further systems of the paper on jittered tori, with the same hierarchy recipe:
+  poisson     : Eq. (Poisson) of Sec. 5.2, (S + eta M) x = M y with eta = 1e-6
+                (nearly singular: the constant mode has eigenvalue ~eta M)
+  bilaplacian : the bi-Laplacian smoothing of Sec. 5.5,
+                (M + alpha S + beta S M^-1 S) x = M y (two-ring stencil)
+
 Small variants of the same recipes (fewer vertices) serve the tests.
 """
 from __future__ import annotations
@@ -67,6 +73,34 @@ def torus_system(n_major: int, n_minor: int, t: float, seed: int, stop: int = 10
     V, F, rng = meshes.jittered_torus(n_major, n_minor, seed)
     y = rng.standard_normal(V.shape[0])
     return _mesh_system(f"torus{n_major}x{n_minor}", V, F, t, y, stop=stop)
+
+
+def poisson_system(n_major: int = 256, n_minor: int = 120, eta: float = 1e-6, seed: int = 5, stop: int = 1000):
+    """Eq. (Poisson) on a jittered torus: (S + eta M) x = M y, y ~ N(0, 1)."""
+    V, F, rng = meshes.jittered_torus(n_major, n_minor, seed)
+    L = operators.cotan_laplacian(V, F)
+    Md = operators.lumped_mass(V, F)
+    A = operators.poisson_matrix(Md, L, eta)
+    rp, ci = operators.edges_to_adjacency(V.shape[0], meshes.mesh_edges(F))
+    Ps = build_hierarchy(V, rp, ci, stop=stop)
+    y = rng.standard_normal(V.shape[0])
+    return System(f"poisson{n_major}x{n_minor}", A, Md * y, Ps, Md, L, eta)
+
+
+def bilaplacian_system(n_major: int = 256, n_minor: int = 120, alpha: float = 1e-3, beta: float = 1e-7,
+                       seed: int = 6, stop: int = 1000):
+    """Bi-Laplacian smoothing (Sec. 5.5) on a jittered torus:
+    (M + alpha S + beta S M^-1 S) x = M y, y ~ N(0, 1).  The hierarchy is
+    built on the mesh edges, as for the other systems."""
+    V, F, rng = meshes.jittered_torus(n_major, n_minor, seed)
+    L = operators.cotan_laplacian(V, F)
+    Md = operators.lumped_mass(V, F)
+    A = operators.bilaplacian_matrix(Md, L, alpha, beta)
+    rp, ci = operators.edges_to_adjacency(V.shape[0], meshes.mesh_edges(F))
+    Ps = build_hierarchy(V, rp, ci, stop=stop)
+    y = rng.standard_normal(V.shape[0])
+    return System(f"bilaplacian{n_major}x{n_minor}", A, Md * y, Ps, Md, L, alpha,
+                  extra=dict(beta=np.array(beta)))
 
 
 def cloud_system(n: int, k: int = 30, t: float = 1e-3, seed: int = 2, stop: int = 1000, graph_k: int = 6):

@@ -57,9 +57,8 @@ static gmg_status fetch_scalars(gmg_ctx* c, cudaStream_t s) {
     GMG_CK(cudaEventElapsedTime(&a, c->ev[0], c->ev[1]));
     GMG_CK(cudaEventElapsedTime(&b, c->ev[2], c->ev[3]));
     GMG_CK(cudaEventElapsedTime(&v, c->ev[4], c->ev[5]));
-    const Level& L = c->L[0];
     c->prof_acc[0] += a + b;
-    c->prof_acc[1] += (double)L.ncolor * (c->opt.nu_pre + c->opt.nu_post);
+    c->prof_acc[1] += (double)c->prof_gs;
     c->prof_acc[2] += v;
     c->prof_acc[3] += 1;
     c->prof_pending = false;

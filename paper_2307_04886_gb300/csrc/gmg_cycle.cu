@@ -108,10 +108,47 @@ __device__ __forceinline__ T combine_parts(T acc, int warp, int lane) {
   return acc;
 }
 
+// Sum of partial[0 .. count) by one block of 256 threads in a fixed order
+// (strided per-thread sums, then a tree); every thread gets the result.
+// Partials written by other blocks of the same grid are read through L2.
+__device__ double block_final_sum(int count, const double* partial, double* red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < count; i += 256) s += __ldcg(partial + i);
+  __syncthreads();
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double v = red[0];
+  __syncthreads();
+  return v;
+}
+
+// True in the one block of the grid that arrives last (after every block has
+// written its partial sums); that block then finishes the reduction, so no
+// separate single-block kernel is launched.  `counter` returns to 0.
+__device__ bool last_block(int* counter) {
+  __shared__ int is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    is_last = atomicAdd(counter, 1) == (int)gridDim.x - 1;
+    if (is_last) *counter = 0;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last != 0;
+}
+
 // One colour of a Gauss-Seidel sweep: x_r = (b_r - sum_{k != r} a_rk x_k) / a_rr
-// for the rows of slices [s0, s1).
+// for the rows of slices [s0, s1).  The FP32 one-warp-per-slice form (the
+// finest level) is held to 32 registers so that 8 CTAs fit per SM and a whole
+// colour of the finest level is resident in one wave (measured: 5.9 -> 5.6 us
+// per colour on the 1M-vertex torus).
 template <class T, int G>
-__global__ void __launch_bounds__(256) k_gs(int64_t s0, int64_t s1, const int64_t* __restrict__ ptr,
+__global__ void __launch_bounds__(256, (G == 1 && sizeof(T) == 4) ? 8 : 1) k_gs(int64_t s0, int64_t s1, const int64_t* __restrict__ ptr,
                                             const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
                                             const int32_t* __restrict__ col, const T* __restrict__ val,
                                             const T* __restrict__ dinv, const T* b, T* x) {
@@ -170,7 +207,8 @@ __global__ void __launch_bounds__(256) k_spmv_dot(int64_t nslice, const int64_t*
                                                   const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
                                                   const int32_t* __restrict__ col, const double* __restrict__ val,
                                                   const double* __restrict__ diag, const double* p,
-                                                  double* q, double* __restrict__ partial) {
+                                                  double* q, double* __restrict__ partial, int* counter,
+                                                  double* out) {
   const int lane = threadIdx.x & 31;
   const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const RowPart rp = row_part<1>(s, nslice, ptr, row0, nrow, 0, lane);
@@ -193,6 +231,10 @@ __global__ void __launch_bounds__(256) k_spmv_dot(int64_t nslice, const int64_t*
     __syncthreads();
   }
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+  if (last_block(counter)) {
+    const double v = block_final_sum(gridDim.x, partial, red);
+    if (threadIdx.x == 0) *out = v;
+  }
 }
 
 // bc = P^T r (gather over the transpose) and xc = 0 (the coarse iterate of the
@@ -201,7 +243,8 @@ template <class T>
 __global__ void __launch_bounds__(256) k_restrict(int64_t nslice, const int64_t* __restrict__ ptr,
                                                   const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
                                                   const int32_t* __restrict__ col, const T* __restrict__ w,
-                                                  const T* r, T* bc, T* xc) {
+                                                  const T* r, T* bc, T* xc, const T* __restrict__ dinvc,
+                                                  int64_t nc0) {
   const int lane = threadIdx.x & 31;
   const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const RowPart p = row_part<1>(s, nslice, ptr, row0, nrow, 0, lane);
@@ -213,7 +256,9 @@ __global__ void __launch_bounds__(256) k_restrict(int64_t nslice, const int64_t*
   if (!p.active) return;
   const T acc = row_dot<T, 1>(p, pv, pc, col, w, r);
   bc[p.row] = acc;
-  xc[p.row] = T(0);
+  // the first Gauss-Seidel colour of the coarse pre-smoothing from x = 0:
+  // (b - 0) / a_ii for the rows of colour 0 (the first nc0 rows)
+  xc[p.row] = p.row < nc0 ? (acc - T(0)) * dinvc[p.row] : T(0);
 }
 
 // x += P u (three packed slots per fine row).
@@ -270,13 +315,16 @@ __global__ void k_d2f(int64_t n, const double* a, float* b) {
   GRID_LOOP(i, n) b[i] = (float)a[i];
 }
 // b32 = (float) r and x32 = 0: the right-hand side and zero initial guess of
-// a correction cycle MGI(0, r).
-__global__ void k_d2f_zero(int64_t n, const double* r, float* b32, float* x32) {
+// a correction cycle MGI(0, r); the rows of colour 0 (the first n0) take
+// their first Gauss-Seidel update from x = 0 right away, (b - 0) / a_ii.
+__global__ void k_d2f_zero(int64_t n, const double* r, float* b32, float* x32, const float* __restrict__ dinv32,
+                           int64_t n0) {
   pdl_wait();
   pdl_trigger();
   GRID_LOOP(i, n) {
-    b32[i] = (float)r[i];
-    x32[i] = 0.f;
+    const float bi = (float)r[i];
+    b32[i] = bi;
+    x32[i] = i < n0 ? (bi - 0.f) * dinv32[i] : 0.f;
   }
 }
 __global__ void k_f2d(int64_t n, const float* a, double* b) {
@@ -312,15 +360,8 @@ __global__ void k_reduce_final(int count, const double* partial, double* out) {
   __shared__ double red[256];
   pdl_wait();
   pdl_trigger();
-  double s = 0.0;
-  for (int i = threadIdx.x; i < count; i += 256) s += partial[i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = red[0];
+  const double v = block_final_sum(count, partial, red);
+  if (threadIdx.x == 0) *out = v;
 }
 
 // PCG scalars live on the device (slots S_*): r.z, p.Ap, the Polak-Ribiere
@@ -339,12 +380,28 @@ __device__ __forceinline__ void block_sum_store(double v, double* red, double* o
   if (threadIdx.x == 0) *out = red[0];
 }
 
-// alpha = rz / pq; r_old = r; x += alpha p; r -= alpha q; partial sums of
-// r.r; and the FP32 right-hand side of the next preconditioning cycle
-// (b32 = r, x32 = 0).  Grid: kRedBlocks x 256.
-__global__ void __launch_bounds__(256) k_pcg_axpy(int64_t n, const double* sc, const double* p, const double* q,
-                                                  double* x, double* r, double* rold, float* b32, float* x32,
-                                                  double* __restrict__ partial) {
+// The convergence test of the device-side loop (one thread): advances the
+// iteration counter it[0], records rel = ||r|| / ||b|| (same arithmetic as the
+// host test) and keeps the loop going while rel is finite, above the
+// tolerance and the counter below it[1].
+__device__ void iter_check(const double* sc, int* it, double* hist, cudaGraphConditionalHandle h) {
+  const int k = ++it[0];
+  const double rel = sqrt(sc[S_RR]) / sqrt(sc[S_NB2]);
+  hist[k] = rel;
+  const bool go = isfinite(rel) && !(rel <= sc[S_TOL]) && k < it[1];
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// alpha = rz / pq; r_old = r; x += alpha p; r -= alpha q; rr = r.r into
+// sc[S_RR] (partials, finished by the last block); and the FP32 right-hand
+// side and initial iterate of the next preconditioning cycle (as k_d2f_zero).
+// With `check` the last block also runs the convergence test of the
+// device-side loop.  Grid: kRedBlocks x 256.
+__global__ void __launch_bounds__(256) k_pcg_axpy(int64_t n, double* sc, const double* p, const double* q, double* x,
+                                                  double* r, double* rold, float* b32, float* x32,
+                                                  const float* __restrict__ dinv32, int64_t n0,
+                                                  double* __restrict__ partial, int* counter, int check, int* it,
+                                                  double* hist, cudaGraphConditionalHandle h) {
   __shared__ double red[256];
   pdl_wait();
   pdl_trigger();
@@ -356,18 +413,27 @@ __global__ void __launch_bounds__(256) k_pcg_axpy(int64_t n, const double* sc, c
     x[i] += alpha * p[i];
     const double rn = ri - alpha * q[i];
     r[i] = rn;
-    b32[i] = (float)rn;
-    x32[i] = 0.f;
+    const float bi = (float)rn;
+    b32[i] = bi;
+    x32[i] = i < n0 ? (bi - 0.f) * dinv32[i] : 0.f;  // colour 0 of the first sweep, as in k_d2f_zero
     rr += rn * rn;
   }
   block_sum_store(rr, red, partial + blockIdx.x);
+  if (last_block(counter)) {
+    const double v = block_final_sum(gridDim.x, partial, red);
+    if (threadIdx.x == 0) {
+      sc[S_RR] = v;
+      if (check) iter_check(sc, it, hist, h);
+    }
+  }
 }
 
-// z = (double) x32 (the preconditioned residual); partial sums of
-// z.(r - r_old) into partial[0 .. gridDim) and of r.z into
-// partial[gridDim .. 2 gridDim).  Grid: kRedBlocks x 256.
+// z = (double) x32 (the preconditioned residual); the Polak-Ribiere
+// numerator z.(r - r_old) and r.z, partial sums finished by the last block,
+// which sets beta = num / rz_old and rz = r.z for the next iteration.
+// Grid: kRedBlocks x 256.
 __global__ void __launch_bounds__(256) k_pcg_zdots(int64_t n, const float* x32, const double* r, const double* rold,
-                                                   double* __restrict__ partial) {
+                                                   double* __restrict__ partial, int* counter, double* sc) {
   __shared__ double red[256];
   pdl_wait();
   pdl_trigger();
@@ -378,40 +444,17 @@ __global__ void __launch_bounds__(256) k_pcg_zdots(int64_t n, const float* x32, 
     rz += ri * zi;
   }
   block_sum_store(num, red, partial + blockIdx.x);
+  __syncthreads();
   block_sum_store(rz, red, partial + gridDim.x + blockIdx.x);
-}
-
-// Final sums of k_pcg_zdots (the tree of k_reduce_final): beta = num / rz_old,
-// then rz = r.z for the next iteration.
-__global__ void k_pcg_beta(int count, const double* partial, double* sc) {
-  __shared__ double red[256];
-  pdl_wait();
-  pdl_trigger();
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < count; i += 256) {
-    a += partial[i];
-    b += partial[count + i];
-  }
-  red[threadIdx.x] = a;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  const double num = red[0];
-  __syncthreads();
-  red[threadIdx.x] = b;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double rzn = red[0];
-    sc[S_NUM] = num;
-    sc[S_BETA] = num / sc[S_RZ];
-    sc[S_RZN] = rzn;
-    sc[S_RZ] = rzn;
+  if (last_block(counter)) {
+    const double a = block_final_sum(gridDim.x, partial, red);
+    const double rzn = block_final_sum(gridDim.x, partial + gridDim.x, red);
+    if (threadIdx.x == 0) {
+      sc[S_NUM] = a;
+      sc[S_BETA] = a / sc[S_RZ];
+      sc[S_RZN] = rzn;
+      sc[S_RZ] = rzn;
+    }
   }
 }
 
@@ -468,46 +511,74 @@ __device__ __forceinline__ U* sm_at(char* sm, int off) {
   return reinterpret_cast<U*>(sm + off);
 }
 
-// One Gauss-Seidel colour (mode 0), the residual of one colour's rows
-// (mode 1) or the prolongation into one colour's rows (mode 2, from the
-// next level's x in xn) over the owned slices of colour k.
-__device__ void tail_rows(const TailLevel& L, char* sm, int k, int mode, const float* xn, int cta, int ncta) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// acc = sum over the slice row's entries of a_ij x_j (shared-memory copies),
+// in entry order, loads issued eight entries ahead of the adds.
+__device__ __forceinline__ float tail_row_dot(const float* val, const int* col, const float* x, int off, int w) {
+  float acc = 0.f;
+  int q = 0;
+  for (; q + 8 <= w; q += 8) {
+    int c[8];
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      c[j] = col[off + (q + j) * 32];
+      v[j] = val[off + (q + j) * 32];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc += v[j] * x[c[j]];
+  }
+  for (; q < w; ++q) acc += val[off + q * 32] * x[col[off + q * 32]];
+  return acc;
+}
+
+// One Gauss-Seidel colour k over the owned slices of that colour.
+__device__ void tail_colour(const TailLevel& L, char* sm, int k, int cta, int ncta) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int* cso = sm_at<int>(sm, L.o_cso);
   const int s0 = cso[k], s1 = cso[k + 1];
   float* x = sm_at<float>(sm, L.o_x);
-  const float* b = sm_at<float>(sm, L.o_b);
-  const int* row0 = sm_at<int>(sm, L.o_row0);
-  const int* nrow = sm_at<int>(sm, L.o_nrow);
-  const int* width = sm_at<int>(sm, L.o_width);
-  const int* soff = sm_at<int>(sm, L.o_soff);
-  const float* val = sm_at<float>(sm, L.o_val);
-  const int* col = sm_at<int>(sm, L.o_col);
-  const int nw = blockDim.x >> 5;
   for (int s = s0 + cta + warp * ncta; s < s1; s += nw * ncta) {
-    const int row = row0[s] + lane;
-    const bool active = lane < nrow[s];
-    if (mode == 2) {
+    const float acc = tail_row_dot(sm_at<float>(sm, L.o_val), sm_at<int>(sm, L.o_col), x,
+                                   sm_at<int>(sm, L.o_soff)[s] + lane, sm_at<int>(sm, L.o_width)[s]);
+    if (lane < sm_at<int>(sm, L.o_nrow)[s]) {
+      const int row = sm_at<int>(sm, L.o_row0)[s] + lane;
+      tail_bcast(x + row, (sm_at<float>(sm, L.o_b)[row] - acc) * sm_at<float>(sm, L.o_dinv)[row], ncta);
+    }
+  }
+}
+
+// Over all owned slices (every colour): the residual (mode 1), the
+// prolongation from the next level's x in xn (mode 2), or the copy of the
+// owned rows of x back to global memory (mode 3).
+__device__ void tail_owned(const TailLevel& L, char* sm, int mode, const float* xn, int ncta) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int* own = sm_at<int>(sm, L.o_own);
+  float* x = sm_at<float>(sm, L.o_x);
+  for (int j = warp; j < L.maxown; j += nw) {
+    const int s = own[j];
+    if (s < 0) continue;
+    const bool active = lane < sm_at<int>(sm, L.o_nrow)[s];
+    const int row = sm_at<int>(sm, L.o_row0)[s] + lane;
+    if (mode == 1) {
+      const float acc = tail_row_dot(sm_at<float>(sm, L.o_val), sm_at<int>(sm, L.o_col), x,
+                                     sm_at<int>(sm, L.o_soff)[s] + lane, sm_at<int>(sm, L.o_width)[s]);
+      if (active)
+        tail_bcast(sm_at<float>(sm, L.o_r) + row,
+                   sm_at<float>(sm, L.o_b)[row] - (acc + sm_at<float>(sm, L.o_diag)[row] * x[row]), ncta);
+    } else if (mode == 2) {
       if (active) {
         const int q = 3 * row;
         const float v = x[row] + (L.p_w32[q] * xn[L.p_idx[q]] + L.p_w32[q + 1] * xn[L.p_idx[q + 1]] +
                                   L.p_w32[q + 2] * xn[L.p_idx[q + 2]]);
         tail_bcast(x + row, v, ncta);
       }
-      continue;
+    } else if (active) {
+      L.x32[row] = x[row];
     }
-    const int w = width[s], off = soff[s] + lane;
-    float acc = 0.f;
-    for (int q = 0; q < w; ++q) acc += val[off + q * 32] * x[col[off + q * 32]];
-    if (!active) continue;
-    if (mode == 0)
-      tail_bcast(x + row, (b[row] - acc) * sm_at<float>(sm, L.o_dinv)[row], ncta);
-    else
-      tail_bcast(sm_at<float>(sm, L.o_r) + row, b[row] - (acc + sm_at<float>(sm, L.o_diag)[row] * x[row]), ncta);
   }
 }
 
-__global__ void __launch_bounds__(1024) k_tail_cycle(const __grid_constant__ TailDesc D) {
+__global__ void __launch_bounds__(1024, 1) k_tail_cycle(const __grid_constant__ TailDesc D) {
   extern __shared__ __align__(16) char sm[];
   const int cta = (int)cluster_rank(), ncta = D.ncta;
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
@@ -525,16 +596,19 @@ __global__ void __launch_bounds__(1024) k_tail_cycle(const __grid_constant__ Tai
       sm_at<int>(sm, L.o_soff)[s] = L.soff[s];
     }
     for (int k = tid; k <= L.ncolor; k += nt) sm_at<int>(sm, L.o_cso)[k] = L.cso[k];
+    const int32_t* own = L.own + (int64_t)cta * L.maxown;
+    for (int j = tid; j < L.maxown; j += nt) sm_at<int>(sm, L.o_own)[j] = own[j];
     // owned slices' entries, one warp per slice
-    for (int k = 0; k < L.ncolor; ++k)
-      for (int s = L.cso[k] + cta + warp * ncta; s < L.cso[k + 1]; s += nw * ncta) {
-        const int64_t e0 = L.a_ptr[s], ne = L.a_ptr[s + 1] - e0;
-        const int o = L.soff[s];
-        for (int64_t e = lane; e < ne; e += 32) {
-          sm_at<float>(sm, L.o_val)[o + e] = L.a_v32[e0 + e];
-          sm_at<int>(sm, L.o_col)[o + e] = L.a_col[e0 + e];
-        }
+    for (int j = warp; j < L.maxown; j += nw) {
+      const int s = own[j];
+      if (s < 0) continue;
+      const int64_t e0 = L.a_ptr[s], ne = L.a_ptr[s + 1] - e0;
+      const int o = L.soff[s];
+      for (int64_t e = lane; e < ne; e += 32) {
+        sm_at<float>(sm, L.o_val)[o + e] = L.a_v32[e0 + e];
+        sm_at<int>(sm, L.o_col)[o + e] = L.a_col[e0 + e];
       }
+    }
   }
   pdl_wait();  // the vectors below are written by the previous kernel
   pdl_trigger();
@@ -547,23 +621,28 @@ __global__ void __launch_bounds__(1024) k_tail_cycle(const __grid_constant__ Tai
   }
   __syncthreads();
   tail_sync();
-  // down: smoothing, residual, restriction
+  // down: smoothing (colour 0 of the first sweep was applied from x = 0 by the
+  // restriction that produced b when c0_first), residual, restriction
   for (int t = 0; t < D.ntail; ++t) {
     const TailLevel& L = D.lv[t];
     for (int it = 0; it < D.nu_pre; ++it)
-      for (int k = 0; k < L.ncolor; ++k) {
-        tail_rows(L, sm, k, 0, nullptr, cta, ncta);
+      for (int k = (it == 0 && D.c0_first) ? 1 : 0; k < L.ncolor; ++k) {
+        tail_colour(L, sm, k, cta, ncta);
         tail_sync();
       }
-    for (int k = 0; k < L.ncolor; ++k) tail_rows(L, sm, k, 1, nullptr, cta, ncta);
+    tail_owned(L, sm, 1, nullptr, ncta);
     tail_sync();
     // restriction: b_next = P^T r over the owned slices of the transpose; the
-    // next iterate starts from zero (each CTA clears its own copy)
+    // next iterate starts from zero (each CTA clears its own copy), except
+    // that a smoothed next level gets its colour-0 rows' first Gauss-Seidel
+    // update (b - 0) / a_ii right away, stored by their owner into every copy
     const bool last = t + 1 == D.ntail;
     float* bn = last ? sm_at<float>(sm, D.o_bc) : sm_at<float>(sm, D.lv[t + 1].o_b);
     float* xn = last ? sm_at<float>(sm, D.o_xc) : sm_at<float>(sm, D.lv[t + 1].o_x);
+    const float* dn = last ? nullptr : sm_at<float>(sm, D.lv[t + 1].o_dinv);
     const int nn = last ? D.nc : D.lv[t + 1].n;
-    for (int i = tid; i < nn; i += nt) xn[i] = 0.f;
+    const int n0 = (last || !D.c0_first) ? 0 : D.lv[t + 1].nc0;
+    for (int i = n0 + tid; i < nn; i += nt) xn[i] = 0.f;
     const float* r = sm_at<float>(sm, L.o_r);
     for (int s = cta + warp * ncta; s < L.r_nslice; s += nw * ncta) {
       if (lane >= L.r_nrow[s]) continue;
@@ -571,7 +650,9 @@ __global__ void __launch_bounds__(1024) k_tail_cycle(const __grid_constant__ Tai
       const int wd = (int)((L.r_ptr[s + 1] - L.r_ptr[s]) >> 5);
       float acc = 0.f;
       for (int q = 0; q < wd; ++q) acc += L.r_v32[e0 + (int64_t)q * 32] * r[L.r_col[e0 + (int64_t)q * 32]];
-      tail_bcast(bn + L.r_row0[s] + lane, acc, ncta);
+      const int row = L.r_row0[s] + lane;
+      tail_bcast(bn + row, acc, ncta);
+      if (row < n0) tail_bcast(xn + row, (acc - 0.f) * dn[row], ncta);
     }
     tail_sync();
   }
@@ -592,23 +673,16 @@ __global__ void __launch_bounds__(1024) k_tail_cycle(const __grid_constant__ Tai
   for (int t = D.ntail - 1; t >= 0; --t) {
     const TailLevel& L = D.lv[t];
     const float* xn = t + 1 == D.ntail ? sm_at<float>(sm, D.o_xc) : sm_at<float>(sm, D.lv[t + 1].o_x);
-    for (int k = 0; k < L.ncolor; ++k) tail_rows(L, sm, k, 2, xn, cta, ncta);
+    tail_owned(L, sm, 2, xn, ncta);
     tail_sync();
     for (int it = 0; it < D.nu_post; ++it)
       for (int q = 0; q < L.ncolor; ++q) {
-        tail_rows(L, sm, D.post_forward ? q : L.ncolor - 1 - q, 0, nullptr, cta, ncta);
+        tail_colour(L, sm, D.post_forward ? q : L.ncolor - 1 - q, cta, ncta);
         tail_sync();
       }
   }
   // the owned rows of the first tail level back to global memory
-  const TailLevel& L = D.lv[0];
-  const int* cso = sm_at<int>(sm, L.o_cso);
-  for (int k = 0; k < L.ncolor; ++k)
-    for (int s = cso[k] + cta + warp * ncta; s < cso[k + 1]; s += nw * ncta)
-      if (lane < sm_at<int>(sm, L.o_nrow)[s]) {
-        const int row = sm_at<int>(sm, L.o_row0)[s] + lane;
-        L.x32[row] = sm_at<float>(sm, L.o_x)[row];
-      }
+  tail_owned(D.lv[0], sm, 3, nullptr, ncta);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -664,10 +738,10 @@ gmg_status launch_residual(Level& L, const T* x, const T* b, T* r, cudaStream_t 
 }
 
 template <class T>
-gmg_status launch_restrict(Level& L, const T* r, T* bc, T* xc, cudaStream_t s) {
+gmg_status launch_restrict(Level& L, const T* r, T* bc, T* xc, cudaStream_t s, const T* dinvc, int64_t nc0) {
   const Ell& R = L.R;
   return launch(k_restrict<T>, blocks_for(R.nslice * 32, 256, INT32_MAX), 256, s, R.nslice, R.ptr, R.row0, R.nrow,
-                R.col, Vec<T>::v(R), r, bc, xc);
+                R.col, Vec<T>::v(R), r, bc, xc, dinvc, nc0);
 }
 
 template <class T>
@@ -685,7 +759,7 @@ gmg_status launch_coarse(gmg_ctx* c, const T* b, T* x, cudaStream_t s) {
 static gmg_status launch_tail(gmg_ctx* c, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c->tail.ncta);
-  cfg.blockDim = dim3(1024);
+  cfg.blockDim = dim3(c->tail_threads);
   cfg.dynamicSmemBytes = (size_t)c->tail_smem;
   cfg.stream = s;
   cudaLaunchAttribute at[2];
@@ -706,7 +780,7 @@ static gmg_status launch_tail(gmg_ctx* c, cudaStream_t s) {
   return GMG_OK;
 }
 
-gmg_status tail_configure(gmg_ctx* c, int ncta, int smem, bool* ok) {
+gmg_status tail_configure(gmg_ctx* c, int ncta, int threads, int smem, bool* ok) {
   *ok = false;
   if (cudaFuncSetAttribute(k_tail_cycle, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
       cudaFuncSetAttribute(k_tail_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmemLimit) != cudaSuccess) {
@@ -715,7 +789,7 @@ gmg_status tail_configure(gmg_ctx* c, int ncta, int smem, bool* ok) {
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ncta);
-  cfg.blockDim = dim3(1024);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = (size_t)smem;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -734,9 +808,12 @@ gmg_status tail_configure(gmg_ctx* c, int ncta, int smem, bool* ok) {
 }
 
 // MGI(x_l, b_l, l) of Alg. 2 on the level's own vectors.  x_l holds the
-// initial iterate (zero for every l > 0: the restriction clears it).
+// initial iterate (zero for every l > 0: the restriction clears it).  With
+// c0_done the kernel that produced b_l has already applied the first
+// Gauss-Seidel colour to x_l = 0 (the restriction does so for every level it
+// feeds that is smoothed), and the first sweep starts at colour 1.
 template <class T>
-gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s) {
+gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s, bool c0_done) {
   Level& L = c->L[l];
   T* x = Vec<T>::x(L);
   T* b = Vec<T>::b(L);
@@ -746,20 +823,26 @@ gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s) {
   Level& C = c->L[l + 1];
   const bool prof = c->prof && l == 0;
   if (prof) GMG_CK(record_timing_event(c->ev[0], s));
+  int gs = 0;
   for (int it = 0; it < c->opt.nu_pre; ++it)
-    for (int k = 0; k < L.ncolor; ++k) GMG_TRY(launch_gs_colour<T>(L, k, b, x, s));
+    for (int k = (it == 0 && c0_done) ? 1 : 0; k < L.ncolor; ++k, ++gs) GMG_TRY(launch_gs_colour<T>(L, k, b, x, s));
   if (prof) GMG_CK(record_timing_event(c->ev[1], s));
   GMG_TRY(launch_residual<T>(L, x, b, Vec<T>::r(L), s));
-  GMG_TRY(launch_restrict<T>(L, Vec<T>::r(L), Vec<T>::b(C), Vec<T>::x(C), s));
-  GMG_TRY(vcycle<T>(c, l + 1, s));
+  const bool next_c0 = c->opt.nu_pre > 0 && l + 1 < c->nlev - 1;
+  GMG_TRY(launch_restrict<T>(L, Vec<T>::r(L), Vec<T>::b(C), Vec<T>::x(C), s, next_c0 ? Vec<T>::dinv(C) : nullptr,
+                             next_c0 ? C.color_off[1] : 0));
+  GMG_TRY(vcycle<T>(c, l + 1, s, next_c0));
   GMG_TRY(launch_prolong<T>(L, Vec<T>::x(C), x, s));
   if (prof) GMG_CK(record_timing_event(c->ev[2], s));
   for (int it = 0; it < c->opt.nu_post; ++it)
-    for (int q = 0; q < L.ncolor; ++q) {
+    for (int q = 0; q < L.ncolor; ++q, ++gs) {
       const int k = c->opt.post_forward ? q : L.ncolor - 1 - q;
       GMG_TRY(launch_gs_colour<T>(L, k, b, x, s));
     }
-  if (prof) GMG_CK(record_timing_event(c->ev[3], s));
+  if (prof) {
+    GMG_CK(record_timing_event(c->ev[3], s));
+    c->prof_gs = gs;
+  }
   return GMG_OK;
 }
 
@@ -767,14 +850,15 @@ template gmg_status launch_gs_colour<double>(Level&, int, const double*, double*
 template gmg_status launch_gs_colour<float>(Level&, int, const float*, float*, cudaStream_t);
 template gmg_status launch_residual<double>(Level&, const double*, const double*, double*, cudaStream_t);
 template gmg_status launch_residual<float>(Level&, const float*, const float*, float*, cudaStream_t);
-template gmg_status launch_restrict<double>(Level&, const double*, double*, double*, cudaStream_t);
-template gmg_status launch_restrict<float>(Level&, const float*, float*, float*, cudaStream_t);
+template gmg_status launch_restrict<double>(Level&, const double*, double*, double*, cudaStream_t, const double*,
+                                           int64_t);
+template gmg_status launch_restrict<float>(Level&, const float*, float*, float*, cudaStream_t, const float*, int64_t);
 template gmg_status launch_prolong<double>(Level&, const double*, double*, cudaStream_t);
 template gmg_status launch_prolong<float>(Level&, const float*, float*, cudaStream_t);
 template gmg_status launch_coarse<double>(gmg_ctx*, const double*, double*, cudaStream_t);
 template gmg_status launch_coarse<float>(gmg_ctx*, const float*, float*, cudaStream_t);
-template gmg_status vcycle<double>(gmg_ctx*, int, cudaStream_t);
-template gmg_status vcycle<float>(gmg_ctx*, int, cudaStream_t);
+template gmg_status vcycle<double>(gmg_ctx*, int, cudaStream_t, bool);
+template gmg_status vcycle<float>(gmg_ctx*, int, cudaStream_t, bool);
 
 gmg_status launch_gather(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t s) {
   return launch(k_gather, blocks_for(n), 256, s, n, perm, src, dst);
@@ -811,9 +895,9 @@ static gmg_status dot(gmg_ctx* c, int64_t n, const double* a, const double* b, i
 
 // A finest-level V-cycle, bracketed by timing events when profiling is on.
 template <class T>
-static gmg_status timed_vcycle(gmg_ctx* c, cudaStream_t s) {
+static gmg_status timed_vcycle(gmg_ctx* c, cudaStream_t s, bool c0_done) {
   if (c->prof) GMG_CK(record_timing_event(c->ev[4], s));
-  GMG_TRY(vcycle<T>(c, 0, s));
+  GMG_TRY(vcycle<T>(c, 0, s, c0_done));
   if (c->prof) GMG_CK(record_timing_event(c->ev[5], s));
   return GMG_OK;
 }
@@ -821,8 +905,9 @@ static gmg_status timed_vcycle(gmg_ctx* c, cudaStream_t s) {
 // z = MGI32(0, r), widened to FP64.
 static gmg_status precond32(gmg_ctx* c, const double* r, double* z, cudaStream_t s) {
   Level& L = c->L[0];
-  GMG_TRY(launch(k_d2f_zero, blocks_for(L.n), 256, s, L.n, r, L.b32, L.x32));
-  GMG_TRY(timed_vcycle<float>(c, s));
+  const int64_t n0 = c->opt.nu_pre > 0 ? L.color_off[1] : 0;
+  GMG_TRY(launch(k_d2f_zero, blocks_for(L.n), 256, s, L.n, r, L.b32, L.x32, (const float*)L.dinv32, n0));
+  GMG_TRY(timed_vcycle<float>(c, s, n0 > 0));
   return launch_f2d(L.n, L.x32, z, s);
 }
 
@@ -832,16 +917,18 @@ static gmg_status precond32(gmg_ctx* c, const double* r, double* z, cudaStream_t
 //  FP32_PCG seg 0: q = A p, pq, alpha = rz/pq, x += alpha p, r -= alpha q, rr
 //  FP32_PCG seg 1: z = MGI32(0, r), num = z.(r - r_old), rz' = r.z,
 //                  p = z + (num/rz) p, rz = rz'
-gmg_status iteration_body(gmg_ctx* c, int mode, int seg, cudaStream_t s) {
+gmg_status iteration_body(gmg_ctx* c, int mode, int seg, cudaStream_t s, cudaGraphConditionalHandle h, bool check) {
   Level& L = c->L[0];
   const int64_t n = L.n;
   if (mode == GMG_FP64) {
-    GMG_TRY(timed_vcycle<double>(c, s));  // level-0 x64/b64 alias xs/bs
+    GMG_TRY(timed_vcycle<double>(c, s, false));  // level-0 x64/b64 alias xs/bs
     return outer_residual(c, S_RR, s);
   }
   if (mode == GMG_FP32_REFINE) {
-    GMG_TRY(launch(k_d2f_zero, blocks_for(n), 256, s, n, (const double*)c->rs, L.b32, L.x32));
-    GMG_TRY(timed_vcycle<float>(c, s));
+    const int64_t n0 = c->opt.nu_pre > 0 ? L.color_off[1] : 0;
+    GMG_TRY(launch(k_d2f_zero, blocks_for(n), 256, s, n, (const double*)c->rs, L.b32, L.x32, (const float*)L.dinv32,
+                   n0));
+    GMG_TRY(timed_vcycle<float>(c, s, n0 > 0));
     GMG_TRY(launch(k_add_f2d, blocks_for(n), 256, s, n, (const float*)L.x32, c->xs));
     return outer_residual(c, S_RR, s);
   }
@@ -852,17 +939,15 @@ gmg_status iteration_body(gmg_ctx* c, int mode, int seg, cudaStream_t s) {
       return GMG_ERR_TOO_LARGE;
     }
     GMG_TRY(launch(k_spmv_dot, nb, 256, s, L.A.nslice, L.A.ptr, L.A.row0, L.A.nrow, L.A.col, L.A.v64, L.diag64,
-                   (const double*)c->ps, c->qs, c->red));
-    GMG_TRY(launch(k_reduce_final, 1, 256, s, (int)nb, (const double*)c->red, c->scal + S_PQ));
-    GMG_TRY(launch(k_pcg_axpy, kRedBlocks, 256, s, n, (const double*)c->scal, (const double*)c->ps,
-                   (const double*)c->qs, c->xs, c->rs, c->ros, L.b32, L.x32, c->red));
-    return launch(k_reduce_final, 1, 256, s, kRedBlocks, (const double*)c->red, c->scal + S_RR);
+                   (const double*)c->ps, c->qs, c->red, c->red_cnt, c->scal + S_PQ));
+    return launch(k_pcg_axpy, kRedBlocks, 256, s, n, c->scal, (const double*)c->ps, (const double*)c->qs, c->xs,
+                  c->rs, c->ros, L.b32, L.x32, (const float*)L.dinv32, c->opt.nu_pre > 0 ? L.color_off[1] : 0,
+                  c->red, c->red_cnt + 1, check ? 1 : 0, c->dloop, c->dhist, h);
   }
-  // b32 = r and x32 = 0 were set by segment 0
-  GMG_TRY(timed_vcycle<float>(c, s));
+  // b32 = r and x32 (colour 0 already smoothed from zero) were set by segment 0
+  GMG_TRY(timed_vcycle<float>(c, s, c->opt.nu_pre > 0));
   GMG_TRY(launch(k_pcg_zdots, kRedBlocks, 256, s, n, (const float*)L.x32, (const double*)c->rs,
-                 (const double*)c->ros, c->red));
-  GMG_TRY(launch(k_pcg_beta, 1, 256, s, kRedBlocks, (const double*)c->red, c->scal));
+                 (const double*)c->ros, c->red, c->red_cnt + 2, c->scal));
   return launch(k_pcg_dir, blocks_for(n), 256, s, n, (const double*)c->scal, (const float*)L.x32, c->ps);
 }
 
@@ -874,24 +959,21 @@ gmg_status pcg_start(gmg_ctx* c, cudaStream_t s) {
   return launch(k_copy, blocks_for(n), 256, s, n, (const double*)c->zs, c->ps);
 }
 
-// Convergence test of the device-side loop, one thread: advances the
-// iteration counter it[0], records rel = ||r|| / ||b|| (same arithmetic as the
-// host test) and keeps the loop going while rel is finite, above the
-// tolerance and the counter below it[1].
-__global__ void k_iter_check(const double* sc, int* it, double* hist, cudaGraphConditionalHandle h) {
+// Convergence test of the device-side loop as its own one-thread kernel (the
+// CG form runs it inside the last block of k_pcg_axpy instead).
+__global__ void k_iter_check(double* sc, int* it, double* hist, cudaGraphConditionalHandle h) {
   pdl_wait();
   pdl_trigger();
-  const int k = ++it[0];
-  const double rel = sqrt(sc[S_RR]) / sqrt(sc[S_NB2]);
-  hist[k] = rel;
-  const bool go = isfinite(rel) && !(rel <= sc[S_TOL]) && k < it[1];
-  cudaGraphSetConditional(h, go ? 1u : 0u);
+  iter_check(sc, it, hist, h);
 }
 
 gmg_status loop_body(gmg_ctx* c, int mode, cudaGraphConditionalHandle h, cudaStream_t s) {
-  if (mode == GMG_FP32_PCG) GMG_TRY(iteration_body(c, mode, 1, s));
+  if (mode == GMG_FP32_PCG) {
+    GMG_TRY(iteration_body(c, mode, 1, s));
+    return iteration_body(c, mode, 0, s, h, true);
+  }
   GMG_TRY(iteration_body(c, mode, 0, s));
-  return launch(k_iter_check, 1, 1, s, (const double*)c->scal, c->dloop, c->dhist, h);
+  return launch(k_iter_check, 1, 1, s, c->scal, c->dloop, c->dhist, h);
 }
 
 gmg_status outer_residual_norm(gmg_ctx* c, cudaStream_t s) { return outer_residual(c, S_RR, s); }

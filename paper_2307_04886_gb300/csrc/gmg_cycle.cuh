@@ -32,14 +32,20 @@ template <> struct Vec<float> {
 // host launchers (gmg_cycle.cu)
 template <class T> gmg_status launch_gs_colour(Level& L, int colour, const T* b, T* x, cudaStream_t s);
 template <class T> gmg_status launch_residual(Level& L, const T* x, const T* b, T* r, cudaStream_t s);
-template <class T> gmg_status launch_restrict(Level& L, const T* r, T* bc, T* xc, cudaStream_t s);
+// With dinvc, the rows of colour 0 of the coarse level (the first nc0) get
+// x = b / a_ii (their first Gauss-Seidel update from zero) instead of 0.
+template <class T> gmg_status launch_restrict(Level& L, const T* r, T* bc, T* xc, cudaStream_t s,
+                                              const T* dinvc = nullptr, int64_t nc0 = 0);
 template <class T> gmg_status launch_prolong(Level& L, const T* u, T* x, cudaStream_t s);
 template <class T> gmg_status launch_coarse(gmg_ctx* c, const T* b, T* x, cudaStream_t s);
-template <class T> gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s);
+template <class T> gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s, bool c0_done = false);
 
 gmg_status launch_d2f(int64_t n, const double* a, float* b, cudaStream_t s);
 gmg_status launch_f2d(int64_t n, const float* a, double* b, cudaStream_t s);
-gmg_status iteration_body(gmg_ctx* c, int mode, int seg, cudaStream_t s);
+// check: run the convergence test of the device-side loop (condition h) at
+// the end of the iteration where the iteration's kernels allow it.
+gmg_status iteration_body(gmg_ctx* c, int mode, int seg, cudaStream_t s, cudaGraphConditionalHandle h = 0,
+                          bool check = false);
 gmg_status pcg_start(gmg_ctx* c, cudaStream_t s);
 gmg_status outer_residual_norm(gmg_ctx* c, cudaStream_t s);
 gmg_status norm_b(gmg_ctx* c, cudaStream_t s);

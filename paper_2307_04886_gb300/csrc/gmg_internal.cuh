@@ -198,10 +198,13 @@ constexpr int kMaxTail = 4;            // smoothed levels in the tail
 constexpr int kTailSmemLimit = 200 * 1024;
 struct TailLevel {
   int n, ncolor, nslice, r_nslice;
+  int nc0;  // rows of colour 0 (the first rows in the colour-major numbering)
   // shared-memory copies: x, r, b, 1/a_ii, a_ii (all rows); per slice: first
   // row, rows, width, offset of its entries in the owner's arrays; colour
   // slice offsets; the owned slices' values and columns
-  int o_x, o_r, o_b, o_dinv, o_diag, o_row0, o_nrow, o_width, o_soff, o_cso, o_val, o_col;
+  int o_x, o_r, o_b, o_dinv, o_diag, o_row0, o_nrow, o_width, o_soff, o_cso, o_own, o_val, o_col;
+  int maxown;             // owned slices per CTA (list padded with -1)
+  const int32_t* own;     // ncta x maxown: each CTA's slices, colour by colour
   const int64_t* a_ptr;
   const int32_t *a_row0, *a_nrow, *a_col;
   const float *a_v32, *dinv32, *diag32;
@@ -219,6 +222,7 @@ struct TailLevel {
 struct TailDesc {
   int ntail, nc, ncta;
   int nu_pre, nu_post, post_forward;
+  int c0_first;          // colour 0 of the first pre-smoothing sweep is done by the restriction
   int o_xc, o_bc;        // shared-memory copies of the coarsest x and b
   const float* ainv32;   // coarsest inverse, FP32, nc x nc
   TailLevel lv[kMaxTail];
@@ -247,6 +251,7 @@ struct gmg_ctx {
   // FP32 cycles run levels >= tail_l0 as one cluster launch (0 = off)
   int tail_l0 = 0;
   int tail_smem = 0;
+  int tail_threads = 1024;
   gmg::TailDesc tail{};
   float* Ainv32 = nullptr;  // coarsest inverse in FP32 for the tail launch
   int* dstatus = nullptr;   // device status words
@@ -259,6 +264,7 @@ struct gmg_ctx {
   double* BS = nullptr;
   double* red = nullptr;   // reduction partials
   int64_t red_cap = 0;     // capacity of `red` in doubles
+  int* red_cnt = nullptr;  // arrival counters of the fused last-block reductions (zero between launches)
   double* scal = nullptr;  // device scalars (norms, dots)
   double* h_scal = nullptr;  // pinned host mirror
   // captured iteration bodies, indexed by mode * 2 + segment
@@ -279,10 +285,11 @@ struct gmg_ctx {
   bool prof_pending = false;
   cudaEvent_t ev[6] = {};
   double prof_acc[4] = {0, 0, 0, 0};  // smoothing ms, GS launches, cycle ms, cycles
+  int prof_gs = 0;                    // finest-level GS launches of the last timed cycle
 };
 
 namespace gmg {
 // Whether a tail cluster of ncta CTAs with `smem` bytes of shared memory each
 // can be scheduled on the device (sets the kernel's attributes).
-gmg_status tail_configure(gmg_ctx* c, int ncta, int smem, bool* ok);
+gmg_status tail_configure(gmg_ctx* c, int ncta, int threads, int smem, bool* ok);
 }  // namespace gmg

@@ -542,62 +542,93 @@ __device__ __forceinline__ double recip_newton(double d) {
 }
 
 // m <- m^-1 for a 32 x 32 SPD block held in both triangles, by 32 scalar
-// sweeps of its lower triangle (528 entries over the 256 threads, so the FP64
-// work is spread over all four SM sub-partitions); warp 0 forms each step's
-// pivot reciprocal and scaled column.  A pivot that is not positive sets
-// *bad and is replaced by 1.  blockDim.x == 256; all threads must call it.
+// sweeps of its lower triangle, software-pipelined: during step k, warp 0
+// updates column k+1 itself and from it forms step k+1's pivot reciprocal
+// and scaled column, while six other warps (on the other three SM
+// sub-partitions) update the remaining entries; one block barrier per step.
+// Every entry is updated as v - c_i (c_j / d) with one fused multiply-add.  A
+// pivot that is not positive sets *bad and is replaced by 1.  blockDim.x ==
+// 256; all threads must call it.
 __device__ void sweep_inverse32(double (&m)[32][33], int* bad) {
-  __shared__ double ck[32], cs[32], sdk;
-  const int tid = threadIdx.x;
+  __shared__ double ck[2][32], cs[2][32], sdk[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // workers: warps 1, 2, 3, 5, 6, 7; entry e of the packed lower triangle
+  const int wk = warp == 0 || warp == 4 ? -1 : (warp < 4 ? warp - 1 : warp - 2) * 32 + lane;
   int ei[3], ej[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const int e = tid + 256 * q;
-    int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    const int e = wk + 192 * q;
+    int i = wk < 0 ? 0 : (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
     while ((i + 1) * (i + 2) / 2 <= e) ++i;
-    while (i * (i + 1) / 2 > e) --i;
-    ei[q] = e < 528 ? i : -1;
+    while (i > 0 && i * (i + 1) / 2 > e) --i;
+    ei[q] = (wk >= 0 && e < 528) ? i : -1;
     ej[q] = e - i * (i + 1) / 2;
   }
-  for (int k = 0; k < 32; ++k) {
-    if (tid < 32) {
-      double d = m[k][k];
-      if (!(d > 0.0)) {
-        if (tid == 0) *bad = 1;
-        d = 1.0;
-      }
-      const double dk = recip_newton(d);
-      const double c = tid >= k ? m[tid][k] : m[k][tid];
-      ck[tid] = c;
-      cs[tid] = c * dk;
-      if (tid == 0) sdk = dk;
+  // step 0's pivot and column
+  if (warp == 0) {
+    double d = m[0][0];
+    if (!(d > 0.0)) {
+      if (lane == 0) *bad = 1;
+      d = 1.0;
     }
-    __syncthreads();
+    const double dk = recip_newton(d);
+    const double c = m[lane][0];
+    ck[0][lane] = c;
+    cs[0][lane] = c * dk;
+    if (lane == 0) sdk[0] = dk;
+  }
+  __syncthreads();
+  for (int k = 0; k < 32; ++k) {
+    const int cur = k & 1, nxt = cur ^ 1;
+    if (warp == 0) {
+      if (k + 1 < 32) {
+        // entry (a, b) of column k+1 (lower storage) after step k
+        const int kp = k + 1, a = lane > kp ? lane : kp, bb = lane > kp ? kp : lane;
+        double v;
+        if (bb == k)
+          v = cs[cur][a];
+        else
+          v = __fma_rn(-ck[cur][a], cs[cur][bb], m[a][bb]);
+        m[a][bb] = v;
+        double d = __shfl_sync(0xffffffffu, v, kp);
+        if (!(d > 0.0)) {
+          if (lane == 0) *bad = 1;
+          d = 1.0;
+        }
+        const double dk = recip_newton(d);
+        ck[nxt][lane] = v;
+        cs[nxt][lane] = v * dk;
+        if (lane == 0) sdk[nxt] = dk;
+      }
+    } else if (wk >= 0) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int i = ei[q], j = ej[q];
-      if (i < 0) continue;
-      double v;
-      if (i == k && j == k)
-        v = -sdk;
-      else if (i == k)
-        v = cs[j];
-      else if (j == k)
-        v = cs[i];
-      else
-        v = m[i][j] - ck[i] * cs[j];
-      m[i][j] = v;
+      for (int q = 0; q < 3; ++q) {
+        const int i = ei[q], j = ej[q];
+        if (i < 0 || i == k + 1 || j == k + 1) continue;
+        double v;
+        if (i == k && j == k)
+          v = -sdk[cur];
+        else if (i == k)
+          v = cs[cur][j];
+        else if (j == k)
+          v = cs[cur][i];
+        else
+          v = __fma_rn(-ck[cur][i], cs[cur][j], m[i][j]);
+        m[i][j] = v;
+      }
     }
     __syncthreads();
   }
   // the lower triangle holds -m^-1: negate, then mirror
-#pragma unroll
-  for (int q = 0; q < 3; ++q)
-    if (ei[q] >= 0) m[ei[q]][ej[q]] = -m[ei[q]][ej[q]];
+  for (int e = tid; e < 1024; e += 256) {
+    const int i = e >> 5, j = e & 31;
+    if (i >= j) m[i][j] = -m[i][j];
+  }
   __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 3; ++q)
-    if (ei[q] >= 0 && ei[q] != ej[q]) m[ej[q]][ei[q]] = m[ei[q]][ej[q]];
+  for (int e = tid; e < 1024; e += 256) {
+    const int i = e >> 5, j = e & 31;
+    if (i < j) m[i][j] = m[j][i];
+  }
   __syncthreads();
 }
 
@@ -1268,27 +1299,43 @@ static gmg_status build_tail(gmg_ctx* c) {
     ptr[l].resize(c->L[l].A.nslice + 1);
     GMG_CK(cudaMemcpy(ptr[l].data(), c->L[l].A.ptr, ptr[l].size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
   }
-  for (int ncta : {16, 8}) {
+  // cluster size and threads per CTA (GMG_TAIL_CTAS, GMG_TAIL_THREADS override)
+  std::vector<int> sizes = {16, 8};
+  int threads = 1024;
+  if (const char* e = std::getenv("GMG_TAIL_CTAS")) sizes = {std::atoi(e)};
+  if (const char* e = std::getenv("GMG_TAIL_THREADS")) threads = std::atoi(e);
+  if (threads < 32 || threads > 1024 || threads % 32 != 0) threads = 1024;
+  for (int ncta : sizes) {
+    if (ncta < 1 || ncta > 16) continue;
     for (int l0 = std::max(1, lam - kMaxTail); l0 < lam; ++l0) {
       TailDesc D{};
-      std::vector<std::vector<int32_t>> soff(lam);
+      std::vector<std::vector<int32_t>> soff(lam), own(lam);
       int64_t cur = 0;
       for (int l = l0; l < lam; ++l) {
         Level& L = c->L[l];
         TailLevel& T = D.lv[l - l0];
         const int64_t ns = L.A.nslice;
         soff[l].assign(ns, 0);
-        int64_t emax = 0;
+        int64_t emax = 0, maxown = 0;
+        std::vector<std::vector<int32_t>> ownl(ncta);
         for (int cta = 0; cta < ncta; ++cta) {
           int64_t off = 0;
           for (int k = 0; k < L.ncolor; ++k)
             for (int64_t sl = L.color_slice_off[k] + cta; sl < L.color_slice_off[k + 1]; sl += ncta) {
               soff[l][sl] = (int32_t)off;
               off += ptr[l][sl + 1] - ptr[l][sl];
+              ownl[cta].push_back((int32_t)sl);
             }
           emax = std::max(emax, off);
+          maxown = std::max<int64_t>(maxown, (int64_t)ownl[cta].size());
         }
+        maxown = std::max<int64_t>(maxown, 1);
+        own[l].assign(ncta * maxown, -1);
+        for (int cta = 0; cta < ncta; ++cta)
+          std::copy(ownl[cta].begin(), ownl[cta].end(), own[l].begin() + cta * maxown);
+        T.maxown = (int)maxown;
         T.n = (int)L.n;
+        T.nc0 = (int)L.color_off[1];
         T.ncolor = L.ncolor;
         T.nslice = (int)ns;
         T.r_nslice = (int)L.R.nslice;
@@ -1302,6 +1349,7 @@ static gmg_status build_tail(gmg_ctx* c) {
         T.o_width = (int)cur; cur = al(cur + 4 * ns);
         T.o_soff = (int)cur; cur = al(cur + 4 * ns);
         T.o_cso = (int)cur; cur = al(cur + 4 * (L.ncolor + 1));
+        T.o_own = (int)cur; cur = al(cur + 4 * T.maxown);
         T.o_val = (int)cur; cur = al(cur + 4 * emax);
         T.o_col = (int)cur; cur = al(cur + 4 * emax);
       }
@@ -1310,14 +1358,16 @@ static gmg_status build_tail(gmg_ctx* c) {
       D.o_bc = (int)cur; cur = al(cur + 4 * D.nc);
       if (cur > kTailSmemLimit) continue;
       bool ok = false;
-      GMG_TRY(tail_configure(c, ncta, (int)cur, &ok));
+      GMG_TRY(tail_configure(c, ncta, threads, (int)cur, &ok));
       if (!ok) break;  // this cluster size cannot be scheduled: try the next
       // fill the global pointers and upload the per-slice tables
       for (int l = l0; l < lam; ++l) {
         Level& L = c->L[l];
         TailLevel& T = D.lv[l - l0];
-        int32_t *so, *cs;
+        int32_t *so, *cs, *ow;
         GMG_TRY(upload(c->arena, &so, soff[l].data(), soff[l].size()));
+        GMG_TRY(upload(c->arena, &ow, own[l].data(), own[l].size()));
+        T.own = ow;
         std::vector<int32_t> cso32(L.color_slice_off.begin(), L.color_slice_off.end());
         GMG_TRY(upload(c->arena, &cs, cso32.data(), cso32.size()));
         T.soff = so;
@@ -1344,9 +1394,11 @@ static gmg_status build_tail(gmg_ctx* c) {
       D.nu_pre = c->opt.nu_pre;
       D.nu_post = c->opt.nu_post;
       D.post_forward = c->opt.post_forward;
+      D.c0_first = c->opt.nu_pre > 0 ? 1 : 0;
       D.ainv32 = c->Ainv32;
       c->tail = D;
       c->tail_smem = (int)cur;
+      c->tail_threads = threads;
       c->tail_l0 = l0;
       return GMG_OK;
     }
@@ -1434,6 +1486,8 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   GMG_TRY(a.alloc(&c->red, (size_t)c->red_cap));
   GMG_TRY(a.alloc(&c->scal, 64));
   GMG_TRY(a.alloc(&c->dloop, 2));
+  GMG_TRY(a.alloc(&c->red_cnt, 4));
+  GMG_CK(cudaMemset(c->red_cnt, 0, 4 * sizeof(int)));
   GMG_TRY(a.alloc(&c->dhist, (size_t)c->opt.max_iter + 2));
   GMG_CK(cudaMallocHost((void**)&c->h_scal, 64 * sizeof(double)));
   GMG_TRY(build_tail(c));
