@@ -204,8 +204,9 @@ gmg_status gmg_destroy_many(gmg_many m);
 gmg_status gmg_destroy(gmg_handle h);
 
 /* Launch-shape autotuner: for every level with Gauss-Seidel sweeps, times
- * four FP32 sweeps with each row split over G = 1, 2, 4 and 8 warps and keeps
- * the fastest G (it also serves the residual).  lanes_out (NULL or nlev - 1
+ * four FP32 sweeps (captured in a CUDA graph, as a solve runs them) with each
+ * row split over G = 1, 2, 4 and 8 warps and keeps the fastest G (it also
+ * serves the residual).  Synchronises `stream` first.  lanes_out (NULL or nlev - 1
  * ints) receives the choices.  The split changes only the summation order of
  * a row.  Call between solves; it drops captured graphs (they are re-captured
  * on the next solve) and overwrites the FP32 work vectors. */

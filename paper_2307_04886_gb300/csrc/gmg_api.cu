@@ -414,40 +414,62 @@ static gmg_status apply_lanes(gmg_handle h) {
 
 gmg_status gmg_autotune(gmg_handle h, int* lanes_out, void* stream) {
   GMG_TRY(check_handle(h));
-  cudaStream_t s = (cudaStream_t)stream;
+  // The sweeps are timed as they run in a solve: captured in a CUDA graph with
+  // programmatic launches, where the cost of a phase depends on its CTA count
+  // and dependent loads rather than on the host's launch rate.
+  GMG_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  if (!h->g_stream) GMG_CK(cudaStreamCreateWithFlags(&h->g_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = h->g_stream;
   cudaEvent_t e0, e1;
   GMG_CK(cudaEventCreate(&e0));
   GMG_CK(cudaEventCreate(&e1));
   gmg_status st = GMG_OK;
+  const uint64_t launches_before = g_launches;
   for (int l = 0; l + 1 < h->nlev && st == GMG_OK; ++l) {
     Level& L = h->L[l];
     const int keep = L.lanes;
     float best_ms = 1e30f;
     int best = keep;
-    if (cudaMemsetAsync(L.x32, 0, sizeof(float) * (size_t)L.n, s) != cudaSuccess ||
-        cudaMemsetAsync(L.b32, 0, sizeof(float) * (size_t)L.n, s) != cudaSuccess) {
+    if (cudaMemsetAsync(L.x32, 0, sizeof(float) * (size_t)L.n, cs) != cudaSuccess ||
+        cudaMemsetAsync(L.b32, 0, sizeof(float) * (size_t)L.n, cs) != cudaSuccess) {
       st = GMG_ERR_CUDA;
       break;
     }
     for (int G : {1, 2, 4, 8}) {
       L.lanes = G;
-      float ms = 0.f;
-      for (int rep = 0; rep < 2 && st == GMG_OK; ++rep) {  // rep 0 warms up
-        cudaEventRecord(e0, s);
-        for (int sweep = 0; sweep < 4 && st == GMG_OK; ++sweep)
-          for (int k = 0; k < L.ncolor && st == GMG_OK; ++k) st = launch_gs_colour<float>(L, k, L.b32, L.x32, s);
-        cudaEventRecord(e1, s);
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        st = GMG_ERR_CUDA;
+        break;
+      }
+      for (int sweep = 0; sweep < 4 && st == GMG_OK; ++sweep)
+        for (int k = 0; k < L.ncolor && st == GMG_OK; ++k) st = launch_gs_colour<float>(L, k, L.b32, L.x32, cs);
+      const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+      if (st == GMG_OK && ec == cudaSuccess && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
+        float ms = 0.f;
+        cudaGraphLaunch(ge, cs);  // warm-up
+        cudaEventRecord(e0, cs);
+        for (int rep = 0; rep < 3; ++rep) cudaGraphLaunch(ge, cs);
+        cudaEventRecord(e1, cs);
         if (cudaEventSynchronize(e1) != cudaSuccess) st = GMG_ERR_CUDA;
         cudaEventElapsedTime(&ms, e0, e1);
+        if (st == GMG_OK && ms < best_ms) {
+          best_ms = ms;
+          best = G;
+        }
+      } else if (st == GMG_OK) {
+        set_error("gmg_autotune: graph capture of the sweeps failed");
+        st = GMG_ERR_CUDA;
       }
-      if (st == GMG_OK && ms < best_ms) {
-        best_ms = ms;
-        best = G;
-      }
+      if (ge) cudaGraphExecDestroy(ge);
+      if (g) cudaGraphDestroy(g);
     }
     L.lanes = st == GMG_OK ? best : keep;
     if (lanes_out) lanes_out[l] = L.lanes;
   }
+  g_launches = launches_before;  // timing launches are not the caller's work
+  cudaStreamSynchronize(cs);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st == GMG_OK) st = apply_lanes(h);
