@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <new>
 #include <vector>
@@ -126,6 +127,7 @@ static gmg_status build_loop(gmg_ctx* c, int mode) {
         return st;
       }
       if (e == cudaSuccess) e = cudaGraphInstantiate(&c->loops[mode], g, 0);
+      if (e == cudaSuccess) c->loop_pdl[mode] = attempt == 0 && use_pdl();
     }
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -134,6 +136,10 @@ static gmg_status build_loop(gmg_ctx* c, int mode) {
     }
   }
   if (!c->loops[mode]) c->loop_refused[mode] = true;
+  if (const char* e = std::getenv("GMG_VERBOSE"))
+    if (e[0] == '1')
+      std::fprintf(stderr, "gmg: device-side loop for mode %d: %s\n", mode,
+                   !c->loops[mode] ? "refused, host loop" : c->loop_pdl[mode] ? "programmatic launches" : "plain stream order");
   return GMG_OK;
 }
 

@@ -275,6 +275,7 @@ struct gmg_ctx {
   cudaGraphExec_t loops[3] = {};
   uint64_t loop_kernels[3] = {};  // kernel nodes of one loop iteration
   bool loop_refused[3] = {};      // instantiation failed: the host loop serves the mode
+  bool loop_pdl[3] = {};          // the loop body kept its programmatic launch edges
   int* dloop = nullptr;           // device iteration counter, iteration limit
   double* dhist = nullptr;        // relative residual per iteration (max_iter + 1)
   cudaStream_t g_stream = nullptr;
