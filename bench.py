@@ -44,6 +44,19 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest value over the ranks of the job (one replica per GPU; the
+    slowest replica sets the job's time), or the value itself with one rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
@@ -303,10 +316,7 @@ def main():
     # per-kernel timing (CUDA events around the finest smoothing blocks and each
     # V-cycle) runs the host-driven loop: event nodes cannot sit in the device loop
     _, _, _, _, pr, _ = timed(solver, 5, 1, prof=True)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
 
     # breakdown (not part of the headline): numeric setup alone
     torch.cuda.synchronize()
