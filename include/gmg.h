@@ -205,14 +205,15 @@ gmg_status gmg_destroy(gmg_handle h);
 
 /* Launch-shape autotuner: for every level with Gauss-Seidel sweeps, times
  * four FP32 sweeps (captured in a CUDA graph, as a solve runs them) with each
- * row split over G = 1, 2, 4 and 8 warps and keeps the fastest G (it also
- * serves the residual).  Synchronises `stream` first.  lanes_out (NULL or nlev - 1
- * ints) receives the choices.  The split changes only the summation order of
+ * row split over G = 1, 2, 4 and 8 warps and keeps the fastest G, then does
+ * the same for the residual, which gets its own split.  Synchronises `stream`
+ * first.  lanes_out (NULL or nlev - 1 ints) receives the Gauss-Seidel choices.  The split changes only the summation order of
  * a row.  Call between solves; it drops captured graphs (they are re-captured
  * on the next solve) and overwrites the FP32 work vectors. */
 gmg_status gmg_autotune(gmg_handle h, int *lanes_out, void *stream);
 
-/* Sets the warps-per-row split of every level with Gauss-Seidel sweeps
+/* Sets the warps-per-row split of every level with Gauss-Seidel sweeps, for
+ * the sweeps and the residual alike
  * (lanes: nlev - 1 ints, each 1, 2, 4 or 8; GMG_ERR_INVALID_ARG otherwise,
  * nothing changed).  A fixed choice, e.g. one made earlier by gmg_autotune,
  * makes the launch sequence independent of timing.  Drops captured graphs

@@ -473,6 +473,41 @@ gmg_status gmg_autotune(gmg_handle h, int* lanes_out, void* stream) {
     }
     L.lanes = st == GMG_OK ? best : keep;
     if (lanes_out) lanes_out[l] = L.lanes;
+    // the residual covers every row at once: its own split, timed the same way
+    const int rkeep = L.rlanes;
+    float rbest_ms = 1e30f;
+    int rbest = rkeep;
+    for (int G : {1, 2, 4, 8}) {
+      if (st != GMG_OK) break;
+      L.rlanes = G;
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        st = GMG_ERR_CUDA;
+        break;
+      }
+      for (int rep = 0; rep < 4 && st == GMG_OK; ++rep) st = launch_residual<float>(L, L.x32, L.b32, L.r32, cs);
+      const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+      if (st == GMG_OK && ec == cudaSuccess && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
+        float ms = 0.f;
+        cudaGraphLaunch(ge, cs);  // warm-up
+        cudaEventRecord(e0, cs);
+        for (int rep = 0; rep < 3; ++rep) cudaGraphLaunch(ge, cs);
+        cudaEventRecord(e1, cs);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = GMG_ERR_CUDA;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st == GMG_OK && ms < rbest_ms) {
+          rbest_ms = ms;
+          rbest = G;
+        }
+      } else if (st == GMG_OK) {
+        set_error("gmg_autotune: graph capture of the residuals failed");
+        st = GMG_ERR_CUDA;
+      }
+      if (ge) cudaGraphExecDestroy(ge);
+      if (g) cudaGraphDestroy(g);
+    }
+    L.rlanes = st == GMG_OK ? rbest : rkeep;
   }
   g_launches = launches_before;  // timing launches are not the caller's work
   cudaStreamSynchronize(cs);
@@ -494,7 +529,7 @@ gmg_status gmg_set_lanes(gmg_handle h, const int* lanes) {
                 " is not 1, 2, 4 or 8");
       return GMG_ERR_INVALID_ARG;
     }
-  for (int l = 0; l + 1 < h->nlev; ++l) h->L[l].lanes = lanes[l];
+  for (int l = 0; l + 1 < h->nlev; ++l) h->L[l].lanes = h->L[l].rlanes = lanes[l];
   return apply_lanes(h);
 }
 

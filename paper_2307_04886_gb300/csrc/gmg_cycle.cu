@@ -720,7 +720,7 @@ gmg_status launch_gs_colour(Level& L, int colour, const T* b, T* x, cudaStream_t
 template <class T>
 static gmg_status launch_residual_p(Level& L, const T* x, const T* b, T* r, double* partial, cudaStream_t s,
                                     int64_t* nblocks = nullptr) {
-  const int G = L.lanes;
+  const int G = L.rlanes;
   const int64_t grid = (L.A.nslice + (8 / G) - 1) / (8 / G);
   if (nblocks) *nblocks = grid;
   const Ell& A = L.A;
@@ -878,7 +878,7 @@ gmg_status launch_f2d(int64_t n, const float* a, double* b, cudaStream_t s) {
 // rs = bs - A xs (FP64, finest level) and scal[slot] = ||rs||^2.
 static gmg_status outer_residual(gmg_ctx* c, int slot, cudaStream_t s) {
   Level& L = c->L[0];
-  const int64_t blocks = (L.A.nslice + (8 / L.lanes) - 1) / (8 / L.lanes);
+  const int64_t blocks = (L.A.nslice + (8 / L.rlanes) - 1) / (8 / L.rlanes);
   if (blocks > c->red_cap) {
     set_error("outer residual: more blocks than reduction partials");
     return GMG_ERR_TOO_LARGE;

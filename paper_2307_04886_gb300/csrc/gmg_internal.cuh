@@ -137,7 +137,8 @@ struct Ell {
 struct Level {
   int64_t n = 0, nnz = 0;
   int ncolor = 0;
-  int lanes = 1;  // warps sharing one row in Gauss-Seidel / residual (1, 2, 4, 8)
+  int lanes = 1;   // warps sharing one row in Gauss-Seidel (1, 2, 4, 8)
+  int rlanes = 1;  // the same for the residual (all rows at once, so more parallel)
   std::vector<int64_t> color_off;        // host: first permuted row of each colour (+ end)
   std::vector<int64_t> color_slice_off;  // host: first slice of each colour (+ end)
   std::vector<int32_t> h_color;          // host: colour of every row (caller numbering)

@@ -895,6 +895,7 @@ static gmg_status build_level_structure(gmg_ctx* c, int l, const int64_t* rp, co
     L.lanes = wavg <= 8.0 ? 1 : wavg <= 16.0 ? 2 : wavg <= 32.0 ? 4 : 8;
     if (const char* e = std::getenv("GMG_LANES")) L.lanes = std::atoi(e);
     if (L.lanes != 1 && L.lanes != 2 && L.lanes != 4 && L.lanes != 8) L.lanes = 1;
+    L.rlanes = L.lanes;
   }
   GMG_TRY(upload(a, &L.csr2ell, c2e.data(), c2e.size()));
   GMG_TRY(upload(a, &L.perm, perm.data(), perm.size()));
