@@ -89,7 +89,7 @@ static void drop_graphs(gmg_ctx* c) {
 
 // Builds the device-side loop of `mode`: a graph holding one conditional
 // WHILE node (condition 1 at every launch) whose body is captured from
-// loop_body.  The body keeps its programmatic launch edges if the driver
+// loop_body.  The body keeps its programmatic launch edges if the CUDA driver
 // instantiates them inside a conditional body, else it is captured again in
 // plain stream order; if neither instantiates, the mode keeps the host loop.
 static gmg_status build_loop(gmg_ctx* c, int mode) {
