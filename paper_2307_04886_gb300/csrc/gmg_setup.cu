@@ -436,7 +436,9 @@ __device__ __forceinline__ void emit_entry(int64_t e, int64_t m, double x, doubl
 // symmetry) into the CSR and the solve layout.  Terms are loaded B at a time
 // before they are added, so a long term list is not a chain of dependent
 // loads: B = 32 for the slices of long entries (hundreds of terms on coarse
-// levels), B = 8 elsewhere (fewer registers, more warps in flight).
+// levels), B = 8 elsewhere (fewer registers, more warps in flight).  The
+// plan is read once, with the evict-first (streaming) hint, so that it does
+// not push the finer level's gathered values out of L2.
 constexpr int kGalThreads = 64;  // small blocks: coarse levels have few entries, and each SM's FP64 pipe counts
 constexpr int kGalLongWidth = 32;  // slices wider than this take the B = 32 kernel
 template <int B>
@@ -459,8 +461,8 @@ __global__ void __launch_bounds__(kGalThreads)
 #pragma unroll
       for (int j = 0; j < B; ++j)
         if (k0 + j < width) {
-          ed[j] = sedge[base + (k0 + j) * 32];
-          cf[j] = scoef[base + (k0 + j) * 32];
+          ed[j] = __ldcs(sedge + base + (k0 + j) * 32);
+          cf[j] = __ldcs(scoef + base + (k0 + j) * 32);
         }
 #pragma unroll
       for (int j = 0; j < B; ++j)
