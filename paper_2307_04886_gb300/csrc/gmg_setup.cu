@@ -435,12 +435,13 @@ __device__ __forceinline__ void emit_entry(int64_t e, int64_t m, double x, doubl
 // plan's order (zero padding adds +0), then written with its mirror (exact
 // symmetry) into the CSR and the solve layout.  Terms are loaded B at a time
 // before they are added, so a long term list is not a chain of dependent
-// loads: B = 32 for the slices of long entries (hundreds of terms on coarse
-// levels), B = 8 elsewhere (fewer registers, more warps in flight).  The
+// loads: B = 16 for the slices of long entries (hundreds of terms on coarse
+// levels; 128 registers, where B = 32 took 226 and halved the warps in
+// flight), B = 8 elsewhere (fewer registers, more warps in flight).  The
 // plan is read once, with the evict-first (streaming) hint, so that it does
 // not push the finer level's gathered values out of L2.
 constexpr int kGalThreads = 64;  // small blocks: coarse levels have few entries, and each SM's FP64 pipe counts
-constexpr int kGalLongWidth = 32;  // slices wider than this take the B = 32 kernel
+constexpr int kGalLongWidth = 32;  // slices wider than this take the B = 16 kernel
 template <int B>
 __global__ void __launch_bounds__(kGalThreads)
     k_gal_level(int64_t g0, int64_t g1, const int32_t* __restrict__ up_entry, const int32_t* __restrict__ mirror,
@@ -1126,7 +1127,7 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s) {
       Level& P = c->L[l - 1];
       const int64_t nsl = F.plan_nup / 32, nlong = F.plan_long_slices;
       if (nlong > 0) {
-        k_gal_level<32><<<grid_for(nlong * 32, kGalThreads, 152 * 128), kGalThreads, 0, s>>>(
+        k_gal_level<16><<<grid_for(nlong * 32, kGalThreads, 152 * 128), kGalThreads, 0, s>>>(
             0, nlong, F.plan_up, F.plan_mirror, F.plan_sptr, F.plan_sedge, F.plan_scoef, P.csr_val, F.csr_val,
             F.csr2ell, F.A.v64, F.A.v32, F.diag64, F.diag32, F.dinv64, F.dinv32, c->dstatus);
         GMG_LAUNCHED();
