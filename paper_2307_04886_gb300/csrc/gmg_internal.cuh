@@ -149,7 +149,7 @@ struct Level {
   int64_t* csr_rowptr = nullptr;
   int32_t* csr_col = nullptr;
   double* csr_val = nullptr;
-  int64_t* csr2ell = nullptr;  // ELL slot of each CSR entry, or -1 - row for the diagonal
+  int64_t* csr2ell = nullptr;  // ELL slot of each CSR entry, or -1 - row for the diagonal (levels > 0)
   // Galerkin plan of this level (l > 0): terms of entry e are
   // plan_edge/plan_coef[plan_ptr[e] .. plan_ptr[e+1]) (CSR positions in level
   // l-1 and P_iJ P_jK), in canonical order; empty below the diagonal

@@ -477,25 +477,40 @@ __global__ void __launch_bounds__(kGalThreads)
 }
 
 // CSR values -> sliced-ELL values, diagonal and inverse diagonal (both
-// precisions).  err bit 1: diagonal <= 0; bit 2: non-finite value.
-__global__ void k_scatter_values(int64_t nnz, const int64_t* __restrict__ csr2ell, const double* __restrict__ v,
-                                 double* __restrict__ e64, float* __restrict__ e32, double* __restrict__ d64,
-                                 float* __restrict__ d32, double* __restrict__ di64, float* __restrict__ di32,
-                                 int* __restrict__ err) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t m = csr2ell[e];
-    const double x = v[e];
-    if (!isfinite(x)) atomicOr(err, 2);
-    if (m >= 0) {
-      e64[m] = x;
-      e32[m] = (float)x;
-    } else {
-      const int64_t r = -1 - m;
-      if (!(x > 0.0)) atomicOr(err, 1);
-      d64[r] = x;
-      d32[r] = (float)x;
-      di64[r] = 1.0 / x;
-      di32[r] = (float)(1.0 / x);
+// precisions), one thread per row of the permuted numbering: the thread of
+// (slice s, lane) walks the CSR row of row0[s] + lane in order and puts its
+// k-th off-diagonal value in slot ptr[s] + 32 k + lane (the slot the layout
+// gives that entry), so a warp stores each slot column as 32 contiguous
+// values and each thread reads one contiguous CSR row.  Padding slots keep
+// their zeros.  err bit 0: diagonal <= 0; bit 1: non-finite value.
+__global__ void k_scatter_rows(int64_t nslice, const int64_t* __restrict__ ptr, const int32_t* __restrict__ row0,
+                               const int32_t* __restrict__ nrow, const int32_t* __restrict__ perm,
+                               const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const double* __restrict__ v, double* __restrict__ e64, float* __restrict__ e32,
+                               double* __restrict__ d64, float* __restrict__ d32, double* __restrict__ di64,
+                               float* __restrict__ di32, int* __restrict__ err) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nslice * 32;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = t >> 5;
+    const int lane = (int)(t & 31);
+    if (lane >= nrow[sl]) continue;
+    const int64_t r = (int64_t)row0[sl] + lane;
+    const int32_t old = perm[r];
+    int64_t slot = ptr[sl] + lane;
+    for (int64_t e = rp[old], e1 = rp[old + 1]; e < e1; ++e) {
+      const double x = v[e];
+      if (!isfinite(x)) atomicOr(err, 2);
+      if (ci[e] == old) {
+        if (!(x > 0.0)) atomicOr(err, 1);
+        d64[r] = x;
+        d32[r] = (float)x;
+        di64[r] = 1.0 / x;
+        di32[r] = (float)(1.0 / x);
+      } else {
+        e64[slot] = x;
+        e32[slot] = (float)x;
+        slot += 32;
+      }
     }
   }
 }
@@ -900,7 +915,7 @@ static gmg_status build_level_structure(gmg_ctx* c, int l, const int64_t* rp, co
     if (L.lanes != 1 && L.lanes != 2 && L.lanes != 4 && L.lanes != 8) L.lanes = 1;
     L.rlanes = L.lanes;
   }
-  GMG_TRY(upload(a, &L.csr2ell, c2e.data(), c2e.size()));
+  if (l > 0) GMG_TRY(upload(a, &L.csr2ell, c2e.data(), c2e.size()));  // level 0 scatters row by row
   GMG_TRY(upload(a, &L.perm, perm.data(), perm.size()));
   GMG_TRY(upload(a, &L.iperm, iperm.data(), iperm.size()));
   GMG_TRY(a.alloc(&L.diag64, n));
@@ -1139,8 +1154,9 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s) {
         GMG_LAUNCHED();
       }
     } else {
-      k_scatter_values<<<grid_for(F.nnz, 256), 256, 0, s>>>(F.nnz, F.csr2ell, F.csr_val, F.A.v64, F.A.v32,
-                                                           F.diag64, F.diag32, F.dinv64, F.dinv32, c->dstatus);
+      k_scatter_rows<<<grid_for(F.A.nslice * 32, 256), 256, 0, s>>>(
+          F.A.nslice, F.A.ptr, F.A.row0, F.A.nrow, F.perm, F.csr_rowptr, F.csr_col, F.csr_val, F.A.v64, F.A.v32,
+          F.diag64, F.diag32, F.dinv64, F.dinv32, c->dstatus);
       GMG_LAUNCHED();
     }
   }
