@@ -29,13 +29,40 @@ _lib = None
 OR_OK, OR_ERR_ARG, OR_ERR_NOT_SPD, OR_ERR_EMPTY_COL, OR_ERR_CHOL, OR_ERR_NOT_CONV = range(6)
 
 
+_LIB_OMP = os.path.join(_HERE, "_gmg_oracle_omp.so")
+_FLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-Wno-unknown-pragmas", "-shared", "-fPIC"]
+
+
 def compile_oracle(force: bool = False) -> str:
+    """The single-threaded build (the one every parity test uses)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp,
-                               _SRC, "-lm"])
+        subprocess.check_call(["gcc", *_FLAGS, "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def compile_oracle_threaded(force: bool = False) -> str | None:
+    """The same source built with -fopenmp: the row loops run on all host
+    cores (OMP_NUM_THREADS to limit them).  Used only for the all-cores CPU
+    baseline.  Returns None when the compiler has no OpenMP runtime."""
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        tmp = _LIB_OMP + f".tmp{os.getpid()}"
+        try:
+            subprocess.check_call(["gcc", *_FLAGS, "-fopenmp", "-o", tmp, _SRC, "-lm"],
+                                  stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (subprocess.CalledProcessError, OSError):
+            return None
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def host_cores() -> int:
+    """Cores available to this process (what the threaded build uses by default)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def compile_variant(src_text: str, out_path: str) -> str:
@@ -44,8 +71,7 @@ def compile_variant(src_text: str, out_path: str) -> str:
     c_path = out_path + ".c"
     with open(c_path, "w") as f:
         f.write(src_text)
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-o", out_path,
-                           c_path, "-lm"])
+    subprocess.check_call(["gcc", *_FLAGS, "-o", out_path, c_path, "-lm"])
     return out_path
 
 
@@ -61,7 +87,7 @@ def _load(path: str | None = None):
         V = ctypes.c_void_p
         lib.or_create.restype = ctypes.c_int
         lib.or_create.argtypes = [ctypes.c_int64, V, V, V, ctypes.c_int, V, V, V, ctypes.c_int, ctypes.c_int,
-                                  ctypes.c_int, V]
+                                  ctypes.c_int, V, V]
         lib.or_destroy.argtypes = [V]
         lib.or_nlev.argtypes = [V]
         lib.or_level_dims.argtypes = [V, ctypes.c_int, V, V, V]
@@ -101,7 +127,9 @@ class Oracle:
     `Ps` (objects with n_coarse, idx [n,3] int32, w [n,3] float64)."""
 
     def __init__(self, A: sp.csr_matrix, Ps, nu_pre: int = 2, nu_post: int = 2, post_forward: bool = False,
-                 lib_path: str | None = None):
+                 lib_path: str | None = None, coloring=None):
+        """`coloring`: None (greedy first-fit colouring on every level) or one
+        entry per level, each None or an int array of colours."""
         lib = _load(lib_path)
         A = sp.csr_matrix(A)
         A.sort_indices()
@@ -115,9 +143,15 @@ class Oracle:
         self._keep += [rp, ci, va, nc] + idx + w
         pidx = (ctypes.c_void_p * max(1, len(Ps)))(*[_p(a).value for a in idx])
         pw = (ctypes.c_void_p * max(1, len(Ps)))(*[_p(a).value for a in w])
+        col = None
+        if coloring is not None:
+            cols = [None if c is None else np.ascontiguousarray(c, dtype=np.int32) for c in coloring]
+            self._keep += cols
+            col = (ctypes.c_void_p * len(cols))(*[None if c is None else _p(c).value for c in cols])
         h = ctypes.c_void_p()
         st = lib.or_create(A.shape[0], _p(rp), _p(ci), _p(va), len(Ps), _p(nc), ctypes.cast(pidx, ctypes.c_void_p),
-                           ctypes.cast(pw, ctypes.c_void_p), nu_pre, nu_post, int(post_forward), ctypes.byref(h))
+                           ctypes.cast(pw, ctypes.c_void_p), nu_pre, nu_post, int(post_forward),
+                           None if col is None else ctypes.cast(col, ctypes.c_void_p), ctypes.byref(h))
         if st != OR_OK:
             raise OracleError(st)
         self._h = h

@@ -32,6 +32,15 @@
  *
  * Compile with -ffp-contract=off so results do not depend on the host's FMA
  * contraction rules.
+ *
+ * The default build is single-threaded.  Built with -fopenmp, the loops over
+ * independent rows (the rows of one colour in a Gauss-Seidel sweep, the rows
+ * of a residual, product or prolongation, the coarse rows of the Galerkin
+ * product, the rows below a Cholesky pivot) run on all host cores with the
+ * same arithmetic per row, so those results are bit-identical to the
+ * single-threaded build; only the dot products and norms of the outer
+ * iteration sum in a thread-dependent order.  The threaded build serves only
+ * as the timed all-cores CPU baseline; the parity tests use the default one.
  */
 #include <math.h>
 #include <stdint.h>
@@ -67,6 +76,21 @@ typedef struct {
 
 static void *xmalloc(size_t n) { return malloc(n ? n : 1); }
 
+/* Rows of each colour, ascending: rows of colour c are crows[cstart[c] ..
+ * cstart[c+1]). */
+static void color_classes(olevel *L) {
+  int64_t n = L->n;
+  int ncolor = L->ncolor;
+  L->cstart = (int64_t *)calloc((size_t)ncolor + 1, sizeof(int64_t));
+  for (int64_t i = 0; i < n; ++i) L->cstart[L->color[i] + 1]++;
+  for (int c = 0; c < ncolor; ++c) L->cstart[c + 1] += L->cstart[c];
+  int64_t *fill = (int64_t *)xmalloc(sizeof(int64_t) * (size_t)ncolor);
+  memcpy(fill, L->cstart, sizeof(int64_t) * (size_t)ncolor);
+  L->crows = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) L->crows[fill[L->color[i]]++] = (int32_t)i;
+  free(fill);
+}
+
 /* Greedy first-fit colouring in increasing row index: row i takes the smallest
  * colour not used by an already coloured neighbour (j < i). */
 static void greedy_color(olevel *L) {
@@ -87,14 +111,26 @@ static void greedy_color(olevel *L) {
   }
   free(mark);
   L->ncolor = ncolor;
-  L->cstart = (int64_t *)calloc((size_t)ncolor + 1, sizeof(int64_t));
-  for (int64_t i = 0; i < n; ++i) L->cstart[L->color[i] + 1]++;
-  for (int c = 0; c < ncolor; ++c) L->cstart[c + 1] += L->cstart[c];
-  int64_t *fill = (int64_t *)xmalloc(sizeof(int64_t) * (size_t)ncolor);
-  memcpy(fill, L->cstart, sizeof(int64_t) * (size_t)ncolor);
-  L->crows = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);
-  for (int64_t i = 0; i < n; ++i) L->crows[fill[L->color[i]]++] = (int32_t)i;
-  free(fill);
+  color_classes(L);
+}
+
+/* A given colouring: every colour in [0, n), no two adjacent rows alike
+ * (otherwise OR_ERR_ARG). */
+static int given_color(olevel *L, const int32_t *color) {
+  int64_t n = L->n;
+  int ncolor = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (color[i] < 0 || color[i] >= n) return OR_ERR_ARG;
+    if (color[i] + 1 > ncolor) ncolor = color[i] + 1;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = L->rowptr[i]; k < L->rowptr[i + 1]; ++k)
+      if (L->col[k] != i && color[L->col[k]] == color[i]) return OR_ERR_ARG;
+  L->color = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);
+  memcpy(L->color, color, sizeof(int32_t) * (size_t)n);
+  L->ncolor = ncolor;
+  color_classes(L);
+  return OR_OK;
 }
 
 static int cmp_i32(const void *a, const void *b) {
@@ -131,41 +167,55 @@ static int galerkin(const olevel *F, olevel *C) {
       }
   free(fill);
 
-  double *acc = (double *)xmalloc(sizeof(double) * (size_t)nc);
-  int64_t *mark = (int64_t *)xmalloc(sizeof(int64_t) * (size_t)nc);
-  for (int64_t K = 0; K < nc; ++K) mark[K] = -1;
-  int32_t *touched = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)nc);
-  int64_t cap = 8 * nc + 16, nnz = 0;
-  int32_t *ccol = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)cap);
-  double *cval = (double *)xmalloc(sizeof(double) * (size_t)cap);
-  int64_t *crp = (int64_t *)xmalloc(sizeof(int64_t) * (size_t)(nc + 1));
-  crp[0] = 0;
-  for (int64_t J = 0; J < nc; ++J) {
-    int64_t nt = 0;
-    for (int64_t q = tp[J]; q < tp[J + 1]; ++q) {
-      int32_t i = ti[q];
-      double wiJ = tw[q];
-      for (int64_t k = F->rowptr[i]; k < F->rowptr[i + 1]; ++k) {
-        int32_t j = F->col[k];
-        double a = F->val[k];
-        for (int s = 0; s < 3; ++s) {
-          double wjK = F->pw[3 * j + s];
-          if (wjK == 0.0) continue;
-          int32_t K = F->pidx[3 * j + s];
-          if (mark[K] != J) { mark[K] = J; acc[K] = 0.0; touched[nt++] = K; }
-          acc[K] = fma(wiJ * wjK, a, acc[K]);
+  /* every coarse row J on its own (private accumulator per thread), kept in
+     a buffer of its own, then concatenated in row order */
+  int32_t **rcol = (int32_t **)xmalloc(sizeof(int32_t *) * (size_t)nc);
+  double **rval = (double **)xmalloc(sizeof(double *) * (size_t)nc);
+  int64_t *rlen = (int64_t *)xmalloc(sizeof(int64_t) * (size_t)nc);
+#pragma omp parallel
+  {
+    double *acc = (double *)xmalloc(sizeof(double) * (size_t)nc);
+    int64_t *mark = (int64_t *)xmalloc(sizeof(int64_t) * (size_t)nc);
+    for (int64_t K = 0; K < nc; ++K) mark[K] = -1;
+    int32_t *touched = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)nc);
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t J = 0; J < nc; ++J) {
+      int64_t nt = 0;
+      for (int64_t q = tp[J]; q < tp[J + 1]; ++q) {
+        int32_t i = ti[q];
+        double wiJ = tw[q];
+        for (int64_t k = F->rowptr[i]; k < F->rowptr[i + 1]; ++k) {
+          int32_t j = F->col[k];
+          double a = F->val[k];
+          for (int s = 0; s < 3; ++s) {
+            double wjK = F->pw[3 * j + s];
+            if (wjK == 0.0) continue;
+            int32_t K = F->pidx[3 * j + s];
+            if (mark[K] != J) { mark[K] = J; acc[K] = 0.0; touched[nt++] = K; }
+            acc[K] = fma(wiJ * wjK, a, acc[K]);
+          }
         }
       }
+      qsort(touched, (size_t)nt, sizeof(int32_t), cmp_i32);
+      rcol[J] = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)nt);
+      rval[J] = (double *)xmalloc(sizeof(double) * (size_t)nt);
+      rlen[J] = nt;
+      for (int64_t q = 0; q < nt; ++q) { rcol[J][q] = touched[q]; rval[J][q] = acc[touched[q]]; }
     }
-    qsort(touched, (size_t)nt, sizeof(int32_t), cmp_i32);
-    if (nnz + nt > cap) {
-      while (nnz + nt > cap) cap *= 2;
-      ccol = (int32_t *)realloc(ccol, sizeof(int32_t) * (size_t)cap);
-      cval = (double *)realloc(cval, sizeof(double) * (size_t)cap);
-    }
-    for (int64_t q = 0; q < nt; ++q) { ccol[nnz] = touched[q]; cval[nnz] = acc[touched[q]]; ++nnz; }
-    crp[J + 1] = nnz;
+    free(acc); free(mark); free(touched);
   }
+  int64_t *crp = (int64_t *)xmalloc(sizeof(int64_t) * (size_t)(nc + 1));
+  crp[0] = 0;
+  for (int64_t J = 0; J < nc; ++J) crp[J + 1] = crp[J] + rlen[J];
+  int64_t nnz = crp[nc];
+  int32_t *ccol = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)nnz);
+  double *cval = (double *)xmalloc(sizeof(double) * (size_t)nnz);
+  for (int64_t J = 0; J < nc; ++J) {
+    memcpy(ccol + crp[J], rcol[J], sizeof(int32_t) * (size_t)rlen[J]);
+    memcpy(cval + crp[J], rval[J], sizeof(double) * (size_t)rlen[J]);
+    free(rcol[J]); free(rval[J]);
+  }
+  free(rcol); free(rval); free(rlen);
   /* mirror: the lower entry takes the upper entry's value */
   for (int64_t J = 0; J < nc; ++J)
     for (int64_t k = crp[J]; k < crp[J + 1]; ++k) {
@@ -179,7 +229,7 @@ static int galerkin(const olevel *F, olevel *C) {
         else { cval[k] = cval[mid]; break; }
       }
     }
-  free(acc); free(mark); free(touched); free(tp); free(ti); free(tw);
+  free(tp); free(ti); free(tw);
   C->n = nc;
   C->nnz = nnz;
   C->rowptr = crp;
@@ -194,24 +244,28 @@ static double diag_of(const olevel *L, int64_t i) {
   return 0.0;
 }
 
-/* Dense Cholesky A = L L^T (Cholesky-Banachiewicz, row by row). */
+/* Dense Cholesky A = L L^T, column by column: L_jj = sqrt(A_jj - sum_{k<j}
+ * L_jk^2), then L_ij = (A_ij - sum_{k<j} L_ik L_jk) / L_jj for i > j (each
+ * sum over k ascending). */
 static int dense_cholesky(const olevel *C, double *Lf) {
   int64_t n = C->n;
   memset(Lf, 0, sizeof(double) * (size_t)(n * n));
   double *Ad = (double *)calloc((size_t)(n * n), sizeof(double));
   for (int64_t i = 0; i < n; ++i)
     for (int64_t k = C->rowptr[i]; k < C->rowptr[i + 1]; ++k) Ad[i * n + C->col[k]] = C->val[k];
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t j = 0; j <= i; ++j) {
+  for (int64_t j = 0; j < n; ++j) {
+    double d = Ad[j * n + j];
+    for (int64_t k = 0; k < j; ++k) d -= Lf[j * n + k] * Lf[j * n + k];
+    if (!(d > 0.0)) { free(Ad); return OR_ERR_CHOL; }
+    const double ljj = sqrt(d);
+    Lf[j * n + j] = ljj;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = j + 1; i < n; ++i) {
       double s = Ad[i * n + j];
       for (int64_t k = 0; k < j; ++k) s -= Lf[i * n + k] * Lf[j * n + k];
-      if (i == j) {
-        if (!(s > 0.0)) { free(Ad); return OR_ERR_CHOL; }
-        Lf[i * n + i] = sqrt(s);
-      } else {
-        Lf[i * n + j] = s / Lf[j * n + j];
-      }
+      Lf[i * n + j] = s / ljj;
     }
+  }
   free(Ad);
   return OR_OK;
 }
@@ -230,10 +284,11 @@ void or_destroy(octx *c) {
 }
 
 /* Setup of Alg. 1: copies A and the prolongations, forms every Galerkin level,
- * colours every level and factors the coarsest one. */
+ * colours every level (the given colouring of a level when `coloring` holds one
+ * for it, else greedy first fit) and factors the coarsest one. */
 int or_create(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val, int nP,
               const int64_t *ncoarse, const int32_t *const *pidx, const double *const *pw,
-              int nu_pre, int nu_post, int post_forward, octx **out) {
+              int nu_pre, int nu_post, int post_forward, const int32_t *const *coloring, octx **out) {
   *out = NULL;
   if (nP < 0 || nP + 1 > OR_MAXLEV || n <= 0) return OR_ERR_ARG;
   octx *c = (octx *)calloc(1, sizeof(octx));
@@ -257,7 +312,11 @@ int or_create(int64_t n, const int64_t *rowptr, const int32_t *col, const double
     F->x = (double *)calloc((size_t)F->n, sizeof(double));
     F->b = (double *)calloc((size_t)F->n, sizeof(double));
     F->r = (double *)calloc((size_t)F->n, sizeof(double));
-    greedy_color(F);
+    if (coloring && coloring[l]) {
+      if (given_color(F, coloring[l])) { or_destroy(c); return OR_ERR_ARG; }
+    } else {
+      greedy_color(F);
+    }
     if (l == nP) break;
     F->nc = ncoarse[l];
     F->pidx = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(3 * F->n));
@@ -306,6 +365,7 @@ void or_smooth(const octx *c, int l, double *x, const double *b, int nsweep, int
   for (int s = 0; s < nsweep; ++s)
     for (int q = 0; q < L->ncolor; ++q) {
       int cc = descending ? L->ncolor - 1 - q : q;
+#pragma omp parallel for schedule(static)
       for (int64_t p = L->cstart[cc]; p < L->cstart[cc + 1]; ++p) {
         int32_t i = L->crows[p];
         double sum = b[i], d = 0.0;
@@ -322,6 +382,7 @@ void or_smooth(const octx *c, int l, double *x, const double *b, int nsweep, int
 /* r = b - A_l x */
 void or_residual(const octx *c, int l, const double *x, const double *b, double *r) {
   const olevel *L = &c->lev[l];
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < L->n; ++i) {
     double s = b[i];
     for (int64_t k = L->rowptr[i]; k < L->rowptr[i + 1]; ++k) s -= L->val[k] * x[L->col[k]];
@@ -332,6 +393,7 @@ void or_residual(const octx *c, int l, const double *x, const double *b, double 
 /* y = A_l x */
 void or_apply(const octx *c, int l, const double *x, double *y) {
   const olevel *L = &c->lev[l];
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < L->n; ++i) {
     double s = 0.0;
     for (int64_t k = L->rowptr[i]; k < L->rowptr[i + 1]; ++k) s += L->val[k] * x[L->col[k]];
@@ -351,6 +413,7 @@ void or_restrict(const octx *c, int l, const double *r, double *bc) {
 /* x += P_l u */
 void or_prolong_add(const octx *c, int l, const double *u, double *x) {
   const olevel *L = &c->lev[l];
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < L->n; ++i)
     for (int s = 0; s < 3; ++s)
       if (L->pw[3 * i + s] != 0.0) x[i] += L->pw[3 * i + s] * u[L->pidx[3 * i + s]];
@@ -388,11 +451,13 @@ void or_mgi(const octx *c, int l, double *x, const double *b) {
 
 static double norm2(const double *v, int64_t n) {
   double s = 0.0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
   for (int64_t i = 0; i < n; ++i) s += v[i] * v[i];
   return sqrt(s);
 }
 static double dotp(const double *a, const double *b, int64_t n) {
   double s = 0.0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
   for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
 }
@@ -447,6 +512,7 @@ int or_solve(const octx *c, int mode, const double *b, double *x, double tol, in
       or_apply(c, 0, p, q); /* q = A p */
       double alpha = rz / dotp(p, q, n);
       memcpy(rold, r, sizeof(double) * (size_t)n);
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
       ++k;
       rel = norm2(r, n) / nb;
@@ -464,9 +530,11 @@ int or_solve(const octx *c, int mode, const double *b, double *x, double tol, in
       memset(z, 0, sizeof(double) * (size_t)n);
       or_mgi(c, 0, z, r);
       double num = 0.0;
+#pragma omp parallel for reduction(+ : num) schedule(static)
       for (int64_t i = 0; i < n; ++i) num += z[i] * (r[i] - rold[i]);
       double beta = num / rz;
       rz = dotp(r, z, n);
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
     }
     free(z); free(p); free(q); free(rold);
