@@ -8,5 +8,5 @@ residuals, transfers, coarse solves), which the oracle and the CUDA library
 each implement on their own.
 """
 from .hierarchy import Prolongation, build_hierarchy, build_level, compile_builder  # noqa: F401
-from .workloads import (System, cached, cloud_system, heat_system, icosphere_system,  # noqa: F401
+from .workloads import (System, cached, cached_batch, cloud_system, heat_system, icosphere_system,  # noqa: F401
                         spheres_batch, torus_system, workload)

@@ -192,6 +192,27 @@ def cached(name: str, maker, *args, **kw) -> System:
     return s
 
 
+def cached_batch(name: str, maker, *args, **kw) -> list:
+    """Like `cached` for a list of systems (one .npz per system under a
+    directory named after the batch)."""
+    d = os.path.join(_CACHE, name)
+    try:
+        with open(os.path.join(d, "count")) as f:
+            count = int(f.read())
+        return [_load(os.path.join(d, f"{k}.npz"), f"{name}_{k}") for k in range(count)]
+    except Exception:
+        pass
+    out = maker(*args, **kw)
+    os.makedirs(d, exist_ok=True)
+    for k, s in enumerate(out):
+        _save(os.path.join(d, f"{k}.npz"), s)
+    tmp = os.path.join(d, f"count.{os.getpid()}")
+    with open(tmp, "w") as f:
+        f.write(str(len(out)))
+    os.replace(tmp, os.path.join(d, "count"))
+    return out
+
+
 def workload(name: str) -> System:
     """The named full-size workloads (see the module docstring)."""
     if name == "icosphere5":

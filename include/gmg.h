@@ -61,8 +61,11 @@ enum {
   GMG_FP32_REFINE = 1, /* FP64 iterative refinement: r = b - A x (FP64),
                           e = MGI(0, r, 1) in FP32 (coarsest solve FP64),
                           x += e; identical to GMG_FP64 in exact arithmetic   */
-  GMG_FP32_PCG = 2     /* FP64 conjugate gradients preconditioned by one FP32
+  GMG_FP32_PCG = 2,    /* FP64 conjugate gradients preconditioned by one FP32
                           V-cycle per iteration (flexible Polak-Ribiere beta)  */
+  GMG_FP64_PCG = 3     /* the same conjugate gradients preconditioned by one
+                          FP64 V-cycle per iteration (separates the gain of CG
+                          from the gain of the FP32 cycle)                     */
 };
 
 enum { GMG_MEM_DEVICE = 0, GMG_MEM_HOST = 1 };
@@ -90,12 +93,13 @@ typedef struct {
 } gmg_prolong;
 
 typedef struct {
-  int precision;  /* GMG_FP64 | GMG_FP32_REFINE | GMG_FP32_PCG (default REFINE) */
+  int precision;  /* GMG_FP64 | GMG_FP32_REFINE | GMG_FP32_PCG | GMG_FP64_PCG
+                     (default REFINE)                                          */
   int nu_pre;     /* Gauss-Seidel sweeps before the coarse correction (2)     */
   int nu_post;    /* sweeps after it (2)                                      */
   int max_iter;   /* outer iterations (100)                                   */
   int post_forward; /* 0: post-relaxation visits colours in descending order
-                       (symmetric cycle, required by GMG_FP32_PCG); 1: ascending */
+                       (symmetric cycle, required by the PCG modes); 1: ascending */
   int use_graphs; /* 1: replay each cycle from a captured CUDA graph (default)  */
 } gmg_options;
 
@@ -119,17 +123,28 @@ const char *gmg_last_error(void);
 /* Alg. 1 setup.  Copies A and the `n_prolong` prolongations (finest first;
  * P[l].n_fine must equal the size of level l), computes every Galerkin level
  * A_{l+1} = P_l^T A_l P_l on the GPU (two-pass symbolic + numeric product,
- * mirrored to exact symmetry), colours every level (greedy first fit in
- * increasing row index), lays the levels out colour by colour, and forms the
- * explicit FP64 inverse of the coarsest level (the direct solve of Alg. 2;
- * block Gauss-Jordan sweeps, every pivot checked positive, which for a
- * symmetric matrix is the Cholesky criterion).  `opt` may be NULL (defaults).
- * On success *h owns all device memory of the hierarchy; release it with
- * gmg_destroy.  Errors: INVALID_ARG, NOT_SPD, EMPTY_P_COLUMN, CHOLESKY,
+ * mirrored to exact symmetry), colours every level, lays the levels out colour
+ * by colour, and forms the explicit FP64 inverse of the coarsest level (the
+ * direct solve of Alg. 2; block Gauss-Jordan sweeps, every pivot checked
+ * positive, which for a symmetric matrix is the Cholesky criterion).
+ *
+ * `coloring` selects the Gauss-Seidel colouring of Sec. 3's relaxation: NULL,
+ * or an array of n_prolong + 1 host pointers, one per level, each NULL (that
+ * level gets the library's greedy first-fit colouring in increasing row
+ * index) or n_l colours in [0, n_l) in the caller's numbering of level l.  No
+ * two adjacent rows of A_l (a stored off-diagonal entry) may share a colour;
+ * pre-relaxation visits the colours in ascending order, post-relaxation in
+ * descending order.  The coarse levels are numbered as the columns of P_l, and
+ * their patterns are those of the Galerkin products (e.g. as the oracle or a
+ * previous gmg_level_export reports them).
+ *
+ * `opt` may be NULL (defaults).  On success *h owns all device memory of the
+ * hierarchy; release it with gmg_destroy.  Errors: INVALID_ARG (also an
+ * improper or out-of-range colouring), NOT_SPD, EMPTY_P_COLUMN, CHOLESKY,
  * NONFINITE, TOO_LARGE (coarsest level above 8192 rows, or a Galerkin row with
  * more than 768 entries), OOM, CUDA. */
 gmg_status gmg_setup(gmg_handle *h, const gmg_csr *A, int n_prolong, const gmg_prolong *P,
-                     const gmg_options *opt, void *stream);
+                     const int32_t *const *coloring, const gmg_options *opt, void *stream);
 
 /* Numeric refresh: new values for A on the SAME sparsity pattern (`val` has
  * rowptr[n] entries in the pattern's order; host or device per `mem`).
@@ -144,22 +159,29 @@ gmg_status gmg_set_values(gmg_handle h, const double *val, int mem, void *stream
 gmg_status gmg_solve(gmg_handle h, const double *b, double *x, double tol, int mem, gmg_solve_info *info,
                      void *stream);
 
-/* Batched right-hand sides: B and X are n x nrhs, row-major (element (i, c)
- * at i * nrhs + c), host or device per `mem`.  Every column is solved to the
- * same tolerance with FP32 V-cycles that read each matrix once for all
- * columns, inside FP64 refinement.  1 <= nrhs <= 16. */
+/* Batched right-hand sides: Alg. 1 (the iteration x <- x + MGI(0, b - A x, 1),
+ * which equals x <- MGI(x, b, 1) in exact arithmetic because the cycle of
+ * Alg. 2 is affine in x) for nrhs systems with the same A at once; the paper
+ * solves one right-hand side at a time, batching is this library's addition.
+ * B and X are n x nrhs, row-major (element (i, c) at i * nrhs + c), host or
+ * device per `mem`.  Every column is solved to the same tolerance with FP32
+ * V-cycles that read each matrix once for all columns, inside FP64
+ * refinement.  1 <= nrhs <= 16.  info->iters counts the outer iterations of
+ * the batch (every column takes part in each). */
 gmg_status gmg_solve_batched(gmg_handle h, int nrhs, const double *B, double *X, double tol, int mem,
                              gmg_solve_info *info, void *stream);
 
 /* ---- A(t) = M + t L kept split (Eq. (smoothing): M lumped mass, L the
  * Laplacian) and the adjoint gradient of a loss of x = A(t)^-1 M u0 ---- */
 
-/* Like gmg_setup for A = M + t L, remembering M (host, n diagonal entries)
- * and L (host CSR; every row must store its diagonal; A shares L's pattern).
+/* Like gmg_setup (colouring included) for A = M + t L, remembering M (host,
+ * n diagonal entries) and L (host CSR; every row must store its diagonal; A
+ * shares L's pattern).
  * Errors: those of gmg_setup, and INVALID_ARG for t < 0 or a missing L
  * diagonal. */
 gmg_status gmg_setup_ML(gmg_handle *h, const double *M_diag, const gmg_csr *L, double t, int n_prolong,
-                        const gmg_prolong *P, const gmg_options *opt, void *stream);
+                        const gmg_prolong *P, const int32_t *const *coloring, const gmg_options *opt,
+                        void *stream);
 
 /* Numeric refresh for a new t: A_1 = M + t L on the GPU, then every
  * Galerkin level and the coarsest factor (as gmg_set_values). */
@@ -177,6 +199,14 @@ gmg_status gmg_mass(gmg_handle h, const double *u, double *out, void *stream);
  * pointers; any output may be NULL.  Requires a handle from gmg_setup_ML. */
 gmg_status gmg_grad(gmg_handle h, const double *lambda, const double *x, double *grad_u0, double *dLdt,
                     double *G_vals, void *stream);
+
+/* The same pattern gradient as gmg_grad without the u0 gradient:
+ * G_vals[k] = -lambda_i x_j for the k-th stored entry (i, j) of L (dloss/dA
+ * on A's pattern, since dA/dt = L the chain rule gives dloss/dt from it) and
+ * *dLdt = -lambda^T L x; either output may be NULL.  Device pointers;
+ * requires a handle from gmg_setup_ML. */
+gmg_status gmg_grad_pattern(gmg_handle h, const double *lambda, const double *x, double *G_vals, double *dLdt,
+                            void *stream);
 
 /* ---- many independent systems (meshes of uneven size) in one batch ---- */
 typedef struct gmg_many_ctx *gmg_many;
@@ -232,6 +262,13 @@ gmg_status gmg_profile(gmg_handle h, int enable);
  * far (each replay of a captured graph counts its kernel nodes). */
 uint64_t gmg_kernel_launches(void);
 gmg_status gmg_profile_read(gmg_handle h, double *out /* 4 */);
+/* Per-level sums over the same timed cycles since the last call (then reset):
+ * out[4l + 0] = ms in level l's Gauss-Seidel sweeps, out[4l + 1] = its colour
+ * launches, out[4l + 2] = ms in its residual, restriction and prolongation,
+ * out[4l + 3] = ms of the whole level including the coarser ones.  A level
+ * run inside the FP32 cycle's cluster tail, or as the coarsest solve, has
+ * only out[4l + 3] (the levels below it report 0).  out: 4 * nlev doubles. */
+gmg_status gmg_profile_levels(gmg_handle h, double *out);
 
 /* ---- introspection (host outputs) ---- */
 gmg_status gmg_num_levels(gmg_handle h, int *nlev);
@@ -260,6 +297,21 @@ gmg_status gmg_prolong_add(gmg_handle h, int l, int fp32, const double *u, doubl
 gmg_status gmg_coarse_solve(gmg_handle h, int fp32, const double *b, double *x, void *stream);
 /* One V-cycle x <- MGI(x, b, 1) of Alg. 2 on the finest level. */
 gmg_status gmg_vcycle(gmg_handle h, int fp32, const double *b, double *x, void *stream);
+/* One FP32 V-cycle X <- MGI(X, B, 1) of Alg. 2 applied to nrhs columns at
+ * once, with the kernels gmg_solve_batched and gmg_solve_many run (each matrix
+ * entry read once for all columns): B and X are device n x nrhs blocks,
+ * row-major in the caller's numbering; X holds the initial iterates and is
+ * overwritten.  Inputs are rounded to FP32; the coarsest solve accumulates in
+ * FP64.  1 <= nrhs <= 16. */
+gmg_status gmg_vcycle_batched(gmg_handle h, int nrhs, const double *B, double *X, void *stream);
+
+/* The reciprocal 1/d that the coarsest inverse (Alg. 2's direct solve) takes
+ * of each pivot: Newton-Raphson iteration r <- r + r (1 - d r) from the FP32
+ * reciprocal, two steps.  Applied elementwise to n device values d (out: n
+ * device values); exposed so that it can be checked against the correctly
+ * rounded division.  Values outside [1e-30, 1e30] in magnitude take the FP64
+ * division. */
+gmg_status gmg_pivot_reciprocal(int64_t n, const double *d, double *out, void *stream);
 
 /* ---- allocation-free residual (no counterpart in the paper) ----
  * For callers that cannot allocate device memory (code running inside
@@ -273,7 +325,10 @@ gmg_status gmg_vcycle(gmg_handle h, int fp32, const double *b, double *x, void *
  * static device array that every GPU loading the library keeps until the
  * process exits, so n is limited to 16,777,216 rows (GMG_ERR_TOO_LARGE
  * beyond).  The first call on a device looks up that array's device address
- * (with the device current): make it before any stream capture.  All calls
+ * (with the device current): make it before any stream capture.  The address
+ * is cached per device and CUDA context; after cudaDeviceReset (a new
+ * context) the next call looks it up again, so that call too belongs before
+ * any capture.  All calls
  * share the array, so calls that overlap on the GPU (other streams, or
  * other host threads on the same device) race and must be serialised by the
  * caller.  Sums run in a fixed order: repeated calls give identical bits. */

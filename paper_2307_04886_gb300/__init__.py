@@ -20,7 +20,7 @@ from .build import LIB, build_library  # noqa: F401
 
 GMG_OK, GMG_ERR_INVALID_ARG, GMG_ERR_NOT_SPD, GMG_ERR_EMPTY_P_COLUMN, GMG_ERR_CHOLESKY, GMG_ERR_NOT_CONVERGED, \
     GMG_ERR_NONFINITE, GMG_ERR_OOM, GMG_ERR_CUDA, GMG_ERR_TIMEOUT, GMG_ERR_TOO_LARGE = range(11)
-GMG_FP64, GMG_FP32_REFINE, GMG_FP32_PCG = 0, 1, 2
+GMG_FP64, GMG_FP32_REFINE, GMG_FP32_PCG, GMG_FP64_PCG = 0, 1, 2, 3
 GMG_MEM_DEVICE, GMG_MEM_HOST = 0, 1
 
 EXPORTED = [
@@ -29,6 +29,7 @@ EXPORTED = [
     "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_coarse_solve", "gmg_vcycle", "gmg_profile",
     "gmg_profile_read", "gmg_kernel_launches", "gmg_residual_norm_noalloc", "gmg_setup_ML", "gmg_set_t",
     "gmg_mass", "gmg_grad", "gmg_setup_many", "gmg_solve_many", "gmg_destroy_many", "gmg_autotune", "gmg_set_lanes",
+    "gmg_vcycle_batched", "gmg_pivot_reciprocal", "gmg_profile_levels", "gmg_grad_pattern",
 ]
 
 
@@ -80,7 +81,7 @@ def load_library(path: str | None = None):
         "gmg_default_options": (None, [V]),
         "gmg_status_string": (ctypes.c_char_p, [I]),
         "gmg_last_error": (ctypes.c_char_p, []),
-        "gmg_setup": (I, [V, V, I, V, V, V]),
+        "gmg_setup": (I, [V, V, I, V, V, V, V]),
         "gmg_set_values": (I, [V, V, I, V]),
         "gmg_solve": (I, [V, V, V, D, I, V, V]),
         "gmg_solve_batched": (I, [V, I, V, V, D, I, V, V]),
@@ -94,10 +95,13 @@ def load_library(path: str | None = None):
         "gmg_prolong_add": (I, [V, I, I, V, V, V]),
         "gmg_coarse_solve": (I, [V, I, V, V, V]),
         "gmg_vcycle": (I, [V, I, V, V, V]),
+        "gmg_vcycle_batched": (I, [V, I, V, V, V]),
+        "gmg_pivot_reciprocal": (I, [I64, V, V, V]),
         "gmg_profile": (I, [V, I]),
         "gmg_kernel_launches": (ctypes.c_uint64, []),
         "gmg_residual_norm_noalloc": (I, [I64, V, V, V, V, V, V, V, V]),
-        "gmg_setup_ML": (I, [V, V, V, D, I, V, V, V]),
+        "gmg_setup_ML": (I, [V, V, V, D, I, V, V, V, V]),
+        "gmg_grad_pattern": (I, [V, V, V, V, V, V]),
         "gmg_set_t": (I, [V, D, V]),
         "gmg_mass": (I, [V, V, V, V]),
         "gmg_grad": (I, [V, V, V, V, V, V, V]),
@@ -107,6 +111,7 @@ def load_library(path: str | None = None):
         "gmg_solve_many": (I, [V, I, V, V, D, I, V, V]),
         "gmg_destroy_many": (I, [V]),
         "gmg_profile_read": (I, [V, V]),
+        "gmg_profile_levels": (I, [V, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -151,9 +156,12 @@ class Solver:
     """
 
     def __init__(self, A, Ps, precision: int = GMG_FP32_REFINE, nu_pre: int = 2, nu_post: int = 2,
-                 max_iter: int = 100, post_forward: bool = False, use_graphs: bool = True, ml=None):
+                 max_iter: int = 100, post_forward: bool = False, use_graphs: bool = True, ml=None,
+                 coloring=None):
         """`ml = (Mdiag, L, t)` builds the hierarchy of A = M + t L with M and L
-        kept split (gmg_setup_ML); A is then ignored."""
+        kept split (gmg_setup_ML); A is then ignored.  `coloring`: None (the
+        library's greedy colouring on every level) or one entry per level,
+        each None or an int array of colours in that level's numbering."""
         import scipy.sparse as sp
 
         lib = load_library()
@@ -178,13 +186,19 @@ class Solver:
             nf = P.n_coarse
         opt = gmg_options(precision, nu_pre, nu_post, max_iter, int(post_forward), int(use_graphs))
         self._opt = opt
+        col = None
+        if coloring is not None:
+            if len(coloring) != len(Ps) + 1:
+                raise ValueError("coloring needs one entry per level")
+            self._col = [None if c is None else np.ascontiguousarray(c, dtype=np.int32) for c in coloring]
+            col = (ctypes.c_void_p * len(self._col))(*[None if c is None else _np_ptr(c).value for c in self._col])
         h = ctypes.c_void_p()
         if ml is not None:
-            _check(lib.gmg_setup_ML(ctypes.byref(h), _np_ptr(self._M), ctypes.byref(csr), self.t, len(Ps), arr,
+            _check(lib.gmg_setup_ML(ctypes.byref(h), _np_ptr(self._M), ctypes.byref(csr), self.t, len(Ps), arr, col,
                                     ctypes.byref(opt), _stream()), "gmg_setup_ML")
         else:
-            _check(lib.gmg_setup(ctypes.byref(h), ctypes.byref(csr), len(Ps), arr, ctypes.byref(opt), _stream()),
-                   "gmg_setup")
+            _check(lib.gmg_setup(ctypes.byref(h), ctypes.byref(csr), len(Ps), arr, col, ctypes.byref(opt),
+                                 _stream()), "gmg_setup")
         self._h = h
         self._lib = lib
         nl = ctypes.c_int()
@@ -305,6 +319,12 @@ class Solver:
         _check(self._lib.gmg_profile_read(self._h, _np_ptr(out)), "gmg_profile_read")
         return tuple(float(v) for v in out)
 
+    def profile_levels(self):
+        """Per level: (smoothing ms, GS launches, transfer ms, whole-level ms) since the last read."""
+        out = np.zeros(4 * self.nlev)
+        _check(self._lib.gmg_profile_levels(self._h, _np_ptr(out)), "gmg_profile_levels")
+        return [tuple(float(v) for v in out[4 * l: 4 * l + 4]) for l in range(self.nlev)]
+
     # ---- introspection ----
     def level(self, l: int):
         """(A_l as scipy CSR in caller numbering, colour of every row)."""
@@ -342,6 +362,13 @@ class Solver:
     def vcycle(self, x, b, fp32=False):
         _check(self._lib.gmg_vcycle(self._h, int(fp32), _dptr(b), _dptr(x), _stream()), "gmg_vcycle")
         return x
+
+    def vcycle_batched(self, X, B):
+        """One FP32 V-cycle on every column of the [n, nrhs] blocks (X in place)."""
+        if B.dim() != 2 or X.shape != B.shape or B.shape[0] != self.n:
+            raise ValueError("expected X and B of shape [n, nrhs]")
+        _check(self._lib.gmg_vcycle_batched(self._h, B.shape[1], _dptr(B), _dptr(X), _stream()), "gmg_vcycle_batched")
+        return X
 
 
 class SolverMany:

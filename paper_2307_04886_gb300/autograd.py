@@ -3,7 +3,9 @@
 
 forward : b = M u0 (gmg_mass), x = A(t)^-1 b (gmg_solve);
 backward: lambda = A(t)^-1 g with the same hierarchy (A is symmetric: the
-          adjoint system is the primal one), then gmg_grad gives
+          adjoint system is the primal one) at the forward's own t (the
+          shared solver is moved back to it if another forward changed it),
+          then gmg_grad gives
           dloss/du0 = M lambda and dloss/dt = -lambda^T L x.
 Only argument marshalling happens here; every step runs in libgmg's kernels.
 """
@@ -21,7 +23,7 @@ class MultigridSmooth(torch.autograd.Function):
         b = solver.mass(u0.contiguous())
         x = torch.zeros_like(b)
         solver.solve(b, x, tol=tol)
-        ctx.solver, ctx.tol = solver, tol
+        ctx.solver, ctx.tol, ctx.t = solver, tol, tv
         ctx.save_for_backward(x)
         return x
 
@@ -29,6 +31,10 @@ class MultigridSmooth(torch.autograd.Function):
     def backward(ctx, g):
         (x,) = ctx.saved_tensors
         solver = ctx.solver
+        # the adjoint system is A(t) of THIS forward: another forward on the
+        # same solver may have moved it to a different t since
+        if solver.t != ctx.t:
+            solver.set_t(ctx.t)
         lam = torch.zeros_like(x)
         solver.solve(g.contiguous(), lam, tol=ctx.tol)
         g_u0, dldt, _ = solver.grad(lam, x)

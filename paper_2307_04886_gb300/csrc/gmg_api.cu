@@ -14,6 +14,8 @@
 namespace gmg {
 extern thread_local std::string g_last_error;
 
+static bool is_pcg(int mode) { return mode == GMG_FP32_PCG || mode == GMG_FP64_PCG; }
+
 static gmg_status check_handle(gmg_handle h) {
   if (!h) {
     set_error("null handle");
@@ -62,6 +64,25 @@ static gmg_status fetch_scalars(gmg_ctx* c, cudaStream_t s) {
     c->prof_acc[1] += (double)c->prof_gs;
     c->prof_acc[2] += v;
     c->prof_acc[3] += 1;
+    for (int l = 0; l < c->nlev && (int)c->lev_ev.size() >= 6 * c->nlev; ++l) {
+      cudaEvent_t* E = &c->lev_ev[6 * l];
+      double* acc = &c->lev_acc[4 * l];
+      float t = 0.f;
+      if (c->lev_kind[l] == 1) {
+        float p0 = 0, p1 = 0, t0 = 0, t1 = 0;
+        GMG_CK(cudaEventElapsedTime(&p0, E[0], E[1]));
+        GMG_CK(cudaEventElapsedTime(&p1, E[4], E[5]));
+        GMG_CK(cudaEventElapsedTime(&t0, E[1], E[2]));
+        GMG_CK(cudaEventElapsedTime(&t1, E[3], E[4]));
+        acc[0] += p0 + p1;
+        acc[1] += c->lev_gs[l];
+        acc[2] += t0 + t1;
+      }
+      if (c->lev_kind[l] != 0) {
+        GMG_CK(cudaEventElapsedTime(&t, E[0], E[5]));
+        acc[3] += t;
+      }
+    }
     c->prof_pending = false;
   }
   return GMG_OK;
@@ -69,7 +90,7 @@ static gmg_status fetch_scalars(gmg_ctx* c, cudaStream_t s) {
 
 static gmg_status run_cycle_body(gmg_ctx* c, int mode, int seg, cudaStream_t s) {
   GMG_TRY(run_body(c, mode, seg, s));
-  if (c->nlev > 1 && (mode != GMG_FP32_PCG || seg == 1)) c->prof_pending = c->prof;
+  if (c->nlev > 1 && (!is_pcg(mode) || seg == 1)) c->prof_pending = c->prof;
   return GMG_OK;
 }
 
@@ -80,7 +101,7 @@ static void drop_graphs(gmg_ctx* c) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
-  for (int m = 0; m < 3; ++m) {
+  for (int m = 0; m < 4; ++m) {
     if (c->loops[m]) cudaGraphExecDestroy(c->loops[m]);
     c->loops[m] = nullptr;
     c->loop_refused[m] = false;
@@ -252,6 +273,8 @@ gmg_status gmg_destroy(gmg_handle h) {
   if (h->g_stream) cudaStreamDestroy(h->g_stream);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : h->lev_ev)
+    if (e) cudaEventDestroy(e);
   if (h->h_scal) cudaFreeHost(h->h_scal);
   cudaDeviceSynchronize();
   h->arena.release();
@@ -259,8 +282,8 @@ gmg_status gmg_destroy(gmg_handle h) {
   return GMG_OK;
 }
 
-gmg_status gmg_setup(gmg_handle* h, const gmg_csr* A, int n_prolong, const gmg_prolong* P, const gmg_options* opt,
-                     void* stream) {
+gmg_status gmg_setup(gmg_handle* h, const gmg_csr* A, int n_prolong, const gmg_prolong* P,
+                     const int32_t* const* coloring, const gmg_options* opt, void* stream) {
   g_last_error.clear();
   if (!h || n_prolong < 0 || (n_prolong > 0 && !P)) {
     set_error("gmg_setup: null output handle or bad prolongation list");
@@ -274,12 +297,12 @@ gmg_status gmg_setup(gmg_handle* h, const gmg_csr* A, int n_prolong, const gmg_p
   if (const char* e = std::getenv("GMG_NO_GRAPHS"))  // profilers list graph nodes slowly
     if (e[0] == '1') c->opt.use_graphs = 0;
   if (c->opt.nu_pre < 0 || c->opt.nu_post < 0 || c->opt.max_iter < 0 || c->opt.precision < GMG_FP64 ||
-      c->opt.precision > GMG_FP32_PCG) {
+      c->opt.precision > GMG_FP64_PCG) {
     set_error("gmg_setup: invalid options");
     delete c;
     return GMG_ERR_INVALID_ARG;
   }
-  gmg_status st = setup_impl(c, A, n_prolong, P, (cudaStream_t)stream);
+  gmg_status st = setup_impl(c, A, n_prolong, P, coloring, (cudaStream_t)stream);
   if (st != GMG_OK) {
     std::string keep = g_last_error;
     gmg_destroy(c);
@@ -341,15 +364,15 @@ gmg_status gmg_solve(gmg_handle h, const double* b, double* x, double tol, int m
       set_error("gmg_solve: non-finite initial residual");
       st = GMG_ERR_NONFINITE;
     } else {
-      if (mode == GMG_FP32_PCG) GMG_TRY(pcg_start(c, s));
+      if (is_pcg(mode)) GMG_TRY(pcg_start(c, mode, s));
       bool fresh = true;  // CG: no step since the (re)start
       while (k < c->opt.max_iter) {
         bool dev = false;
-        if (!(mode == GMG_FP32_PCG && fresh)) GMG_TRY(device_loop_ready(c, mode, &dev));
+        if (!(is_pcg(mode) && fresh)) GMG_TRY(device_loop_ready(c, mode, &dev));
         if (dev) {
           GMG_TRY(run_loop(c, mode, tol, &k, info, s));
         } else {
-          if (mode == GMG_FP32_PCG && !fresh) GMG_TRY(run_cycle_body(c, mode, 1, s));
+          if (is_pcg(mode) && !fresh) GMG_TRY(run_cycle_body(c, mode, 1, s));
           GMG_TRY(run_cycle_body(c, mode, 0, s));
           GMG_TRY(fetch_scalars(c, s));
           ++k;
@@ -361,7 +384,7 @@ gmg_status gmg_solve(gmg_handle h, const double* b, double* x, double tol, int m
           st = GMG_ERR_NONFINITE;
           break;
         }
-        if (rel <= tol && mode == GMG_FP32_PCG) {  // confirm on the true residual
+        if (rel <= tol && is_pcg(mode)) {  // confirm on the true residual
           GMG_TRY(outer_residual_norm(c, s));
           GMG_TRY(fetch_scalars(c, s));
           rel = std::sqrt(c->h_scal[S_RR]) / nb;
@@ -370,7 +393,7 @@ gmg_status gmg_solve(gmg_handle h, const double* b, double* x, double tol, int m
             st = GMG_OK;
             break;
           }
-          GMG_TRY(pcg_start(c, s));  // restart from the current iterate
+          GMG_TRY(pcg_start(c, mode, s));  // restart from the current iterate
           fresh = true;
           continue;
         }
@@ -396,6 +419,13 @@ gmg_status gmg_profile(gmg_handle h, int enable) {
   if ((enable != 0) == h->prof) return GMG_OK;
   if (enable && !h->ev[0])
     for (auto& e : h->ev) GMG_CK(cudaEventCreate(&e));
+  if (enable && h->lev_ev.empty()) {
+    h->lev_ev.assign(6 * h->nlev, nullptr);
+    for (auto& e : h->lev_ev) GMG_CK(cudaEventCreate(&e));
+    h->lev_kind.assign(h->nlev, 0);
+    h->lev_gs.assign(h->nlev, 0);
+    h->lev_acc.assign(4 * h->nlev, 0.0);
+  }
   drop_graphs(h);  // re-capture with or without the event nodes
   h->prof = enable != 0;
   h->prof_pending = false;
@@ -407,6 +437,16 @@ gmg_status gmg_profile_read(gmg_handle h, double* out) {
   for (int k = 0; k < 4; ++k) {
     out[k] = h->prof_acc[k];
     h->prof_acc[k] = 0.0;
+  }
+  return GMG_OK;
+}
+
+gmg_status gmg_profile_levels(gmg_handle h, double* out) {
+  if (!h || !out) return GMG_ERR_INVALID_ARG;
+  const bool have = (int)h->lev_acc.size() >= 4 * h->nlev;
+  for (int k = 0; k < 4 * h->nlev; ++k) {
+    out[k] = have ? h->lev_acc[k] : 0.0;
+    if (have) h->lev_acc[k] = 0.0;
   }
   return GMG_OK;
 }

@@ -8,6 +8,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <string>
 
 #include "gmg_cycle.cuh"
@@ -273,8 +275,12 @@ static inline int gblk(int64_t n) { return (int)std::max<int64_t>(1, std::min<in
 
 #define LCK() GMG_LAUNCHED()
 
+// MGI(X_l, B_l, l) on [n_l x NR] blocks.  Every level starts from X_l = 0
+// (the recursive calls of Alg. 2, and the correction cycle of the outer
+// refinement on the finest level) unless keep_x, which keeps the caller's
+// initial iterate in the finest level's X32.
 template <int NR>
-static gmg_status vcycle_m(gmg_ctx* c, int l, cudaStream_t s) {
+static gmg_status vcycle_m(gmg_ctx* c, int l, cudaStream_t s, bool keep_x = false) {
   Level& L = c->L[l];
   if (l == c->nlev - 1) {
     k_coarse_m<NR><<<(int)((L.n * 32 + 255) / 256), 256, 0, s>>>((int)L.n, c->Ainv, L.B32, L.X32);
@@ -282,7 +288,7 @@ static gmg_status vcycle_m(gmg_ctx* c, int l, cudaStream_t s) {
     return GMG_OK;
   }
   Level& C = c->L[l + 1];
-  GMG_CK(cudaMemsetAsync(L.X32, 0, sizeof(float) * (size_t)(L.n * NR), s));
+  if (!keep_x) GMG_CK(cudaMemsetAsync(L.X32, 0, sizeof(float) * (size_t)(L.n * NR), s));
   auto sweep = [&](int k) -> gmg_status {
     const int64_t s0 = L.color_slice_off[k], s1 = L.color_slice_off[k + 1];
     if (s1 > s0)
@@ -468,26 +474,121 @@ extern "C" gmg_status gmg_solve_batched(gmg_handle h, int nrhs, const double* B,
   return solve_m<16>(h, nrhs, B, X, tol, mem, info, s);
 }
 
+namespace gmg {
+// One FP32 multi-right-hand-side V-cycle on the finest level, X <- MGI32(X, B):
+// caller-numbered FP64 blocks in, rounded to FP32, the cycle, widened back.
+template <int NR>
+static gmg_status vcycle_step_m(gmg_ctx* c, int nrhs, const double* B, double* X, cudaStream_t s) {
+  Level& L0 = c->L[0];
+  const int64_t n = L0.n;
+  k_gather_m<<<gblk(n * NR), 256, 0, s>>>(n, nrhs, NR, L0.perm, B, c->BS);
+  LCK();
+  k_gather_m<<<gblk(n * NR), 256, 0, s>>>(n, nrhs, NR, L0.perm, X, c->XS);
+  LCK();
+  GMG_TRY(launch_d2f(n * NR, c->BS, L0.B32, s));
+  GMG_TRY(launch_d2f(n * NR, c->XS, L0.X32, s));
+  GMG_TRY(vcycle_m<NR>(c, 0, s, true));
+  GMG_TRY(launch_f2d(n * NR, L0.X32, c->XS, s));
+  k_scatter_m<<<gblk(n * nrhs), 256, 0, s>>>(n, nrhs, NR, L0.perm, c->XS, X);
+  LCK();
+  return GMG_OK;
+}
+}  // namespace gmg
+
+extern "C" gmg_status gmg_vcycle_batched(gmg_handle h, int nrhs, const double* B, double* X, void* stream) {
+  if (!h || !B || !X || nrhs < 1 || nrhs > kMaxRhs) {
+    set_error("gmg_vcycle_batched: bad handle, block or nrhs (1..16)");
+    return GMG_ERR_INVALID_ARG;
+  }
+  GMG_CK(cudaSetDevice(h->device));
+  GMG_TRY(ensure_batched(h));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nrhs == 1) return vcycle_step_m<1>(h, nrhs, B, X, s);
+  if (nrhs == 2) return vcycle_step_m<2>(h, nrhs, B, X, s);
+  if (nrhs <= 4) return vcycle_step_m<4>(h, nrhs, B, X, s);
+  if (nrhs <= 8) return vcycle_step_m<8>(h, nrhs, B, X, s);
+  return vcycle_step_m<16>(h, nrhs, B, X, s);
+}
+
 // ------------------------------------------------------------------ many meshes
 // A batch of independent systems (meshes of uneven size), each with its own
-// hierarchy and nrhs right-hand sides.  Every outer iteration is ONE graph
-// launch whose branches run each mesh's multi-right-hand-side FP32 V-cycle,
-// FP64 correction and FP64 residual concurrently; one host synchronisation
-// per iteration reads every mesh's column norms.
+// hierarchy and nrhs right-hand sides.  The whole solve is ONE graph launch:
+// a conditional WHILE node repeats an iteration in which a gate kernel opens
+// one conditional IF node per mesh that has not converged yet; the IF bodies
+// (each mesh's multi-right-hand-side FP32 V-cycle, FP64 correction and FP64
+// residual with column norms) run concurrently, and a check kernel then
+// updates every mesh's relative residual, iteration count and done flag and
+// decides whether the loop goes on.  The host reads the per-mesh results once
+// at the end.  Where the CUDA driver refuses the conditional graph, one graph
+// per iteration with every mesh's branch and a host-side test is used instead.
 
 struct gmg_many_ctx {
   std::vector<gmg_handle> h;
   cudaStream_t cap = nullptr;
   std::vector<cudaStream_t> br;
   std::vector<cudaEvent_t> ev;
-  cudaGraphExec_t graph[5] = {};  // by NR = 1, 2, 4, 8, 16
+  cudaGraphExec_t graph[5] = {};  // host-driven form, by NR = 1, 2, 4, 8, 16
   uint64_t graph_kernels[5] = {};
+  cudaGraphExec_t loop[5] = {};  // device-side loop, by NR
+  uint64_t loop_kernels[5] = {};  // kernel nodes of one loop iteration (all meshes open)
+  bool loop_refused[5] = {};
+  // device state of the device-side loop
+  int* d_state = nullptr;        // [0] iterations done, [1] limit, [2] non-finite seen; then per mesh: done, iters
+  double* d_nb = nullptr;        // per mesh kMaxRhs column norms of B (0: column unused or zero)
+  double* d_rel = nullptr;       // per mesh worst relative residual
+  double* d_tol = nullptr;
+  double** d_rr = nullptr;       // per mesh: its squared column norms of R (the handle's scal + 8)
+  cudaGraphConditionalHandle* d_if = nullptr;  // per mesh IF handle (for the current NR's loop)
+  std::vector<cudaGraphConditionalHandle> h_if[5];
 };
 
 namespace gmg {
 
 static int nr_slot(int NR) { return NR == 1 ? 0 : NR == 2 ? 1 : NR == 4 ? 2 : NR == 8 ? 3 : 4; }
 
+// Opens the IF node of every mesh that is not done.
+__global__ void k_many_gate(int K, const int* __restrict__ state, const cudaGraphConditionalHandle* __restrict__ hif) {
+  for (int k = threadIdx.x; k < K; k += blockDim.x) cudaGraphSetConditional(hif[k], state[3 + 2 * k] ? 0u : 1u);
+}
+
+// After an iteration: every mesh that ran gets its worst column's relative
+// residual and one more iteration, and is done once that is <= tol (a
+// non-finite residual ends the whole loop).  The loop continues while a mesh
+// is not done and the iteration limit is not reached.  One block.
+__global__ void k_many_check(int K, int nrhs, int* state, const double* __restrict__ nb, double* rel,
+                             const double* tol, double* const* rr, cudaGraphConditionalHandle hw) {
+  __shared__ int open, bad;
+  if (threadIdx.x == 0) {
+    open = 0;
+    bad = 0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    int* st = state + 3 + 2 * k;
+    if (st[0]) continue;
+    double w = 0.0;
+    bool fin = true;
+    for (int q = 0; q < nrhs; ++q) {
+      const double b = nb[k * kMaxRhs + q];
+      const double r = b > 0.0 ? sqrt(rr[k][q]) / b : 0.0;
+      if (!isfinite(r)) fin = false;
+      w = fmax(w, r);
+    }
+    st[1] += 1;
+    rel[k] = fin ? w : (double)NAN;
+    if (!fin) atomicOr(&bad, 1);
+    if (fin && w <= *tol) st[0] = 1;
+    else atomicOr(&open, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int it = ++state[0];
+    if (bad) state[2] = 1;
+    cudaGraphSetConditional(hw, (open && !bad && it < state[1]) ? 1u : 0u);
+  }
+}
+
+// The host-driven form: one graph per iteration with every mesh's branch.
 template <int NR>
 static gmg_status many_graph(gmg_many_ctx* m, cudaGraphExec_t* out, uint64_t* kernels) {
   const int K = (int)m->h.size();
@@ -517,12 +618,91 @@ static gmg_status many_graph(gmg_many_ctx* m, cudaGraphExec_t* out, uint64_t* ke
   return GMG_OK;
 }
 
+// The device-side loop: WHILE { gate -> IF_k { iteration of mesh k } for all k -> check }.
+template <int NR>
+static gmg_status many_loop(gmg_many_ctx* m, int slot, int nrhs) {
+  const int K = (int)m->h.size();
+  cudaGraph_t g = nullptr;
+  GMG_CK(cudaGraphCreate(&g, 0));
+  cudaError_t e = cudaSuccess;
+  gmg_status st = GMG_OK;
+  const uint64_t before = g_launches;
+  cudaGraphConditionalHandle hw = 0;
+  cudaGraphNodeParams wp = {};
+  cudaGraphNode_t wnode;
+  e = cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
+  }
+  cudaGraph_t body = e == cudaSuccess ? wp.conditional.phGraph_out[0] : nullptr;
+  std::vector<cudaGraphConditionalHandle>& hif = m->h_if[slot];
+  hif.assign(K, 0);
+  std::vector<cudaGraphNode_t> ifn(K);
+  cudaGraphNode_t gate = nullptr, check = nullptr;
+  // gate kernel node (handles are filled into d_if before every launch of this loop)
+  if (e == cudaSuccess) {
+    cudaKernelNodeParams kp = {};
+    void* args[] = {(void*)&K, (void*)&m->d_state, (void*)&m->d_if};
+    kp.func = (void*)k_many_gate;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&gate, body, nullptr, 0, &kp);
+  }
+  for (int k = 0; k < K && e == cudaSuccess && st == GMG_OK; ++k) {
+    e = cudaGraphConditionalHandleCreate(&hif[k], body, 0, 0);
+    if (e != cudaSuccess) break;
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hif[k];
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    e = cudaGraphAddNode(&ifn[k], body, &gate, nullptr, 1, &ip);
+    if (e != cudaSuccess) break;
+    e = cudaStreamBeginCaptureToGraph(m->br[k], ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    st = iteration_m<NR>(m->h[k], m->br[k]);
+    cudaGraph_t cg = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(m->br[k], &cg);
+    if (e == cudaSuccess) e = ec;
+  }
+  if (e == cudaSuccess && st == GMG_OK) {
+    cudaKernelNodeParams kp = {};
+    void* args[] = {(void*)&K, (void*)&nrhs, (void*)&m->d_state, (void*)&m->d_nb, (void*)&m->d_rel,
+                    (void*)&m->d_tol, (void*)&m->d_rr, (void*)&hw};
+    kp.func = (void*)k_many_check;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&check, body, ifn.data(), (size_t)K, &kp);
+  }
+  m->loop_kernels[slot] = g_launches - before + 2;
+  g_launches = before;
+  if (st == GMG_OK && e == cudaSuccess) e = cudaGraphInstantiate(&m->loop[slot], g, 0);
+  cudaGraphDestroy(g);
+  if (st != GMG_OK) return st;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    m->loop[slot] = nullptr;
+    m->loop_refused[slot] = true;
+    if (const char* v = std::getenv("GMG_VERBOSE"))
+      if (v[0] == '1') std::fprintf(stderr, "gmg: many-mesh device loop refused (%s), host loop\n", cudaGetErrorString(e));
+  }
+  return GMG_OK;
+}
+
 template <int NR>
 static gmg_status many_solve(gmg_many_ctx* m, int nrhs, const double* const* B, double* const* X, double tol,
                              int mem, gmg_solve_info* info, cudaStream_t s) {
   const int K = (int)m->h.size();
-  std::vector<std::vector<double>> nb(K, std::vector<double>(NR, 0.0));
+  std::vector<double> nb((size_t)K * kMaxRhs, 0.0);
   std::vector<double> rel(K, 0.0);
+  std::vector<int> iters(K, 0), done(K, 0);
   // right-hand sides and initial guesses into every hierarchy's permuted layout
   for (int k = 0; k < K; ++k) {
     gmg_ctx* c = m->h[k];
@@ -554,8 +734,8 @@ static gmg_status many_solve(gmg_many_ctx* m, int nrhs, const double* const* B, 
     GMG_CK(cudaStreamSynchronize(s));
     int zmask = 0;
     for (int q = 0; q < nrhs; ++q) {
-      nb[k][q] = std::sqrt(c->h_scal[8 + q]);
-      if (nb[k][q] == 0.0) zmask |= 1 << q;
+      nb[(size_t)k * kMaxRhs + q] = std::sqrt(c->h_scal[8 + q]);
+      if (nb[(size_t)k * kMaxRhs + q] == 0.0) zmask |= 1 << q;
     }
     if (zmask) {
       k_zero_cols<<<gblk(n * NR), 256, 0, s>>>(n, NR, zmask, c->XS);
@@ -563,6 +743,8 @@ static gmg_status many_solve(gmg_many_ctx* m, int nrhs, const double* const* B, 
     }
     GMG_TRY(outer_m<NR>(c, s));
   }
+  // host-side residuals of every mesh not yet done (a done mesh keeps the
+  // residual it converged with)
   auto fetch = [&]() -> gmg_status {
     for (int k = 0; k < K; ++k) {
       gmg_ctx* c = m->h[k];
@@ -570,9 +752,11 @@ static gmg_status many_solve(gmg_many_ctx* m, int nrhs, const double* const* B, 
     }
     GMG_CK(cudaStreamSynchronize(s));
     for (int k = 0; k < K; ++k) {
+      if (done[k]) continue;
       double w = 0.0;
       for (int q = 0; q < nrhs; ++q) {
-        const double r = nb[k][q] > 0 ? std::sqrt(m->h[k]->h_scal[8 + q]) / nb[k][q] : 0.0;
+        const double b = nb[(size_t)k * kMaxRhs + q];
+        const double r = b > 0 ? std::sqrt(m->h[k]->h_scal[8 + q]) / b : 0.0;
         w = std::isfinite(r) ? std::max(w, r) : r;
         if (!std::isfinite(r)) break;
       }
@@ -582,29 +766,71 @@ static gmg_status many_solve(gmg_many_ctx* m, int nrhs, const double* const* B, 
   };
   GMG_TRY(fetch());
   const int slot = nr_slot(NR);
-  int it = 0, max_iter = 0;
+  int max_iter = 0;
   for (auto* c : m->h) max_iter = std::max(max_iter, c->opt.max_iter);
   gmg_status st = GMG_ERR_NOT_CONVERGED;
-  auto done = [&]() {
-    for (int k = 0; k < K; ++k)
-      if (!(rel[k] <= tol)) return false;
-    return true;
-  };
-  auto bad = [&]() {
-    for (int k = 0; k < K; ++k)
-      if (!std::isfinite(rel[k])) return true;
-    return false;
-  };
-  if (bad()) st = GMG_ERR_NONFINITE;
-  else if (done()) st = GMG_OK;
-  while (st == GMG_ERR_NOT_CONVERGED && it < max_iter) {
-    if (!m->graph[slot]) GMG_TRY(many_graph<NR>(m, &m->graph[slot], &m->graph_kernels[slot]));
-    GMG_CK(cudaGraphLaunch(m->graph[slot], s));
-    g_launches += m->graph_kernels[slot];
-    ++it;
-    GMG_TRY(fetch());
-    if (bad()) st = GMG_ERR_NONFINITE;
-    else if (done()) st = GMG_OK;
+  bool bad = false, open = false;
+  for (int k = 0; k < K; ++k) {
+    if (!std::isfinite(rel[k])) bad = true;
+    done[k] = rel[k] <= tol;
+    if (!done[k]) open = true;
+  }
+  if (bad) st = GMG_ERR_NONFINITE;
+  else if (!open) st = GMG_OK;
+  static const bool no_loop = [] {
+    const char* v = std::getenv("GMG_NO_DEVICE_LOOP");
+    return v && v[0] == '1';
+  }();
+  if (st == GMG_ERR_NOT_CONVERGED && max_iter > 0 && !no_loop && !m->loop_refused[slot] && !m->loop[slot])
+    GMG_TRY(many_loop<NR>(m, slot, nrhs));
+  if (st == GMG_ERR_NOT_CONVERGED && max_iter > 0 && m->loop[slot]) {
+    // device-side loop: state, norms and the IF handles of this loop, one launch
+    std::vector<int> hs(3 + 2 * K, 0);
+    hs[1] = max_iter;
+    for (int k = 0; k < K; ++k) hs[3 + 2 * k] = done[k];
+    GMG_CK(cudaMemcpyAsync(m->d_state, hs.data(), sizeof(int) * hs.size(), cudaMemcpyHostToDevice, s));
+    GMG_CK(cudaMemcpyAsync(m->d_nb, nb.data(), sizeof(double) * nb.size(), cudaMemcpyHostToDevice, s));
+    GMG_CK(cudaMemcpyAsync(m->d_tol, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
+    GMG_CK(cudaMemcpyAsync(m->d_rel, rel.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
+    GMG_CK(cudaMemcpyAsync(m->d_if, m->h_if[slot].data(), sizeof(cudaGraphConditionalHandle) * K,
+                           cudaMemcpyHostToDevice, s));
+    GMG_CK(cudaGraphLaunch(m->loop[slot], s));
+    GMG_CK(cudaMemcpyAsync(hs.data(), m->d_state, sizeof(int) * hs.size(), cudaMemcpyDeviceToHost, s));
+    GMG_CK(cudaMemcpyAsync(rel.data(), m->d_rel, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+    GMG_CK(cudaStreamSynchronize(s));
+    uint64_t ran = 0;
+    for (int k = 0; k < K; ++k) {
+      iters[k] = hs[4 + 2 * k];
+      done[k] = hs[3 + 2 * k];
+      ran += (uint64_t)iters[k];
+    }
+    // kernels run: per mesh-iteration its share of the body, plus gate and check per iteration
+    g_launches += (uint64_t)hs[0] * 2 + (K > 0 ? ran * ((m->loop_kernels[slot] - 2) / (uint64_t)K) : 0);
+    bool all = true;
+    for (int k = 0; k < K; ++k) all = all && done[k];
+    st = hs[2] ? GMG_ERR_NONFINITE : all ? GMG_OK : GMG_ERR_NOT_CONVERGED;
+  } else if (st == GMG_ERR_NOT_CONVERGED) {
+    // host-driven form: every mesh iterates until all have converged; a
+    // mesh's count is the iteration at which it first met the tolerance
+    int it = 0;
+    while (st == GMG_ERR_NOT_CONVERGED && it < max_iter) {
+      if (!m->graph[slot]) GMG_TRY(many_graph<NR>(m, &m->graph[slot], &m->graph_kernels[slot]));
+      GMG_CK(cudaGraphLaunch(m->graph[slot], s));
+      g_launches += m->graph_kernels[slot];
+      ++it;
+      GMG_TRY(fetch());
+      bool all = true;
+      for (int k = 0; k < K; ++k) {
+        if (!std::isfinite(rel[k])) bad = true;
+        if (!done[k]) {
+          iters[k] = it;
+          done[k] = rel[k] <= tol;
+        }
+        all = all && done[k];
+      }
+      if (bad) st = GMG_ERR_NONFINITE;
+      else if (all) st = GMG_OK;
+    }
   }
   for (int k = 0; k < K; ++k) {
     gmg_ctx* c = m->h[k];
@@ -615,7 +841,7 @@ static gmg_status many_solve(gmg_many_ctx* m, int nrhs, const double* const* B, 
     if (mem == GMG_MEM_HOST)
       GMG_CK(cudaMemcpyAsync(X[k], c->RS, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToHost, s));
     if (info) {
-      info[k].iters = it;
+      info[k].iters = iters[k];
       info[k].rel_res = rel[k];
     }
   }
@@ -631,6 +857,11 @@ extern "C" gmg_status gmg_destroy_many(gmg_many m) {
   if (!m) return GMG_OK;
   for (auto& g : m->graph)
     if (g) cudaGraphExecDestroy(g);
+  for (auto& g : m->loop)
+    if (g) cudaGraphExecDestroy(g);
+  for (void* p : {(void*)m->d_state, (void*)m->d_nb, (void*)m->d_rel, (void*)m->d_tol, (void*)m->d_rr,
+                  (void*)m->d_if})
+    if (p) cudaFree(p);
   for (auto e : m->ev)
     if (e) cudaEventDestroy(e);
   for (auto s : m->br)
@@ -651,7 +882,7 @@ extern "C" gmg_status gmg_setup_many(gmg_many* out, int nmesh, const gmg_csr* A,
   gmg_many_ctx* m = new gmg_many_ctx();
   for (int k = 0; k < nmesh; ++k) {
     gmg_handle h = nullptr;
-    gmg_status st = gmg_setup(&h, &A[k], n_prolong[k], P[k], opt, stream);
+    gmg_status st = gmg_setup(&h, &A[k], n_prolong[k], P[k], nullptr, opt, stream);
     if (st == GMG_OK) st = ensure_batched(h);
     if (st != GMG_OK) {
       std::string keep = gmg_last_error();
@@ -671,6 +902,18 @@ extern "C" gmg_status gmg_setup_many(gmg_many* out, int nmesh, const gmg_csr* A,
   m->ev.assign(nmesh + 1, nullptr);
   for (int k = 0; ok && k < nmesh; ++k) ok = ck(cudaStreamCreateWithFlags(&m->br[k], cudaStreamNonBlocking));
   for (int k = 0; ok && k <= nmesh; ++k) ok = ck(cudaEventCreateWithFlags(&m->ev[k], cudaEventDisableTiming));
+  // device state of the device-side loop
+  if (ok) ok = ck(cudaMalloc(&m->d_state, sizeof(int) * (size_t)(3 + 2 * nmesh)));
+  if (ok) ok = ck(cudaMalloc(&m->d_nb, sizeof(double) * (size_t)nmesh * kMaxRhs));
+  if (ok) ok = ck(cudaMalloc(&m->d_rel, sizeof(double) * (size_t)nmesh));
+  if (ok) ok = ck(cudaMalloc(&m->d_tol, sizeof(double)));
+  if (ok) ok = ck(cudaMalloc(&m->d_rr, sizeof(double*) * (size_t)nmesh));
+  if (ok) ok = ck(cudaMalloc(&m->d_if, sizeof(cudaGraphConditionalHandle) * (size_t)nmesh));
+  if (ok) {
+    std::vector<double*> rr(nmesh);
+    for (int k = 0; k < nmesh; ++k) rr[k] = m->h[k]->scal + 8;
+    ok = ck(cudaMemcpy(m->d_rr, rr.data(), sizeof(double*) * (size_t)nmesh, cudaMemcpyHostToDevice));
+  }
   if (!ok) {
     gmg_destroy_many(m);
     return GMG_ERR_CUDA;

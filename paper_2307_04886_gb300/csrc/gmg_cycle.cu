@@ -393,13 +393,17 @@ __device__ void iter_check(const double* sc, int* it, double* hist, cudaGraphCon
 }
 
 // alpha = rz / pq; r_old = r; x += alpha p; r -= alpha q; rr = r.r into
-// sc[S_RR] (partials, finished by the last block); and the FP32 right-hand
-// side and initial iterate of the next preconditioning cycle (as k_d2f_zero).
+// sc[S_RR] (partials, finished by the last block); and the initial iterate of
+// the next preconditioning cycle MGI(0, r): with an FP32 cycle its right-hand
+// side b32 = (float) r and x32 (as k_d2f_zero), with an FP64 cycle (which
+// reads r itself as its right-hand side) z64.  The rows of colour 0 (the
+// first n0) take their first Gauss-Seidel update from zero, (r - 0) / a_ii.
 // With `check` the last block also runs the convergence test of the
 // device-side loop.  Grid: kRedBlocks x 256.
+template <class Z>
 __global__ void __launch_bounds__(256) k_pcg_axpy(int64_t n, double* sc, const double* p, const double* q, double* x,
-                                                  double* r, double* rold, float* b32, float* x32,
-                                                  const float* __restrict__ dinv32, int64_t n0,
+                                                  double* r, double* rold, float* b32, Z* z0,
+                                                  const Z* __restrict__ dinv, int64_t n0,
                                                   double* __restrict__ partial, int* counter, int check, int* it,
                                                   double* hist, cudaGraphConditionalHandle h) {
   __shared__ double red[256];
@@ -413,9 +417,13 @@ __global__ void __launch_bounds__(256) k_pcg_axpy(int64_t n, double* sc, const d
     x[i] += alpha * p[i];
     const double rn = ri - alpha * q[i];
     r[i] = rn;
-    const float bi = (float)rn;
-    b32[i] = bi;
-    x32[i] = i < n0 ? (bi - 0.f) * dinv32[i] : 0.f;  // colour 0 of the first sweep, as in k_d2f_zero
+    if constexpr (sizeof(Z) == 4) {
+      const float bi = (float)rn;
+      b32[i] = bi;
+      z0[i] = i < n0 ? (bi - 0.f) * dinv[i] : 0.f;
+    } else {
+      z0[i] = i < n0 ? (rn - 0.0) * dinv[i] : 0.0;
+    }
     rr += rn * rn;
   }
   block_sum_store(rr, red, partial + blockIdx.x);
@@ -428,18 +436,19 @@ __global__ void __launch_bounds__(256) k_pcg_axpy(int64_t n, double* sc, const d
   }
 }
 
-// z = (double) x32 (the preconditioned residual); the Polak-Ribiere
-// numerator z.(r - r_old) and r.z, partial sums finished by the last block,
-// which sets beta = num / rz_old and rz = r.z for the next iteration.
-// Grid: kRedBlocks x 256.
-__global__ void __launch_bounds__(256) k_pcg_zdots(int64_t n, const float* x32, const double* r, const double* rold,
+// z = the preconditioned residual (the cycle's output, FP32 or FP64); the
+// Polak-Ribiere numerator z.(r - r_old) and r.z, partial sums finished by the
+// last block, which sets beta = num / rz_old and rz = r.z for the next
+// iteration.  Grid: kRedBlocks x 256.
+template <class Z>
+__global__ void __launch_bounds__(256) k_pcg_zdots(int64_t n, const Z* z, const double* r, const double* rold,
                                                    double* __restrict__ partial, int* counter, double* sc) {
   __shared__ double red[256];
   pdl_wait();
   pdl_trigger();
   double num = 0.0, rz = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
-    const double zi = (double)x32[i], ri = r[i];
+    const double zi = (double)z[i], ri = r[i];
     num += zi * (ri - rold[i]);
     rz += ri * zi;
   }
@@ -458,12 +467,21 @@ __global__ void __launch_bounds__(256) k_pcg_zdots(int64_t n, const float* x32, 
   }
 }
 
-// p = z + beta p with z = (double) x32.
-__global__ void k_pcg_dir(int64_t n, const double* sc, const float* x32, double* p) {
+// p = z + beta p.
+template <class Z>
+__global__ void k_pcg_dir(int64_t n, const double* sc, const Z* z, double* p) {
   pdl_wait();
   pdl_trigger();
   const double beta = sc[S_BETA];
-  GRID_LOOP(i, n) p[i] = (double)x32[i] + beta * p[i];
+  GRID_LOOP(i, n) p[i] = (double)z[i] + beta * p[i];
+}
+// z = 0 with the rows of colour 0 (the first n0) at their first Gauss-Seidel
+// update from zero, (r - 0) / a_ii: the start of an FP64 correction cycle
+// MGI(0, r) that reads r as its right-hand side.
+__global__ void k_zero_c0(int64_t n, const double* r, double* z, const double* __restrict__ dinv, int64_t n0) {
+  pdl_wait();
+  pdl_trigger();
+  GRID_LOOP(i, n) z[i] = i < n0 ? (r[i] - 0.0) * dinv[i] : 0.0;
 }
 __global__ void k_copy(int64_t n, const double* a, double* b) {
   pdl_wait();
@@ -813,27 +831,47 @@ gmg_status tail_configure(gmg_ctx* c, int ncta, int threads, int smem, bool* ok)
 // Gauss-Seidel colour to x_l = 0 (the restriction does so for every level it
 // feeds that is smoothed), and the first sweep starts at colour 1.
 template <class T>
-gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s, bool c0_done) {
+gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s, bool c0_done, T* x_in, const T* b_in) {
   Level& L = c->L[l];
-  T* x = Vec<T>::x(L);
-  T* b = Vec<T>::b(L);
-  if (l == c->nlev - 1) return launch_coarse<T>(c, b, x, s);
-  if constexpr (std::is_same<T, float>::value)
-    if (c->tail_l0 > 0 && l == c->tail_l0) return launch_tail(c, s);
+  T* x = x_in ? x_in : Vec<T>::x(L);
+  const T* b = b_in ? b_in : Vec<T>::b(L);
+  const bool lp = c->prof && (int)c->lev_ev.size() >= 6 * c->nlev;  // per-level events
+  cudaEvent_t* E = lp ? &c->lev_ev[6 * l] : nullptr;
+  bool whole = l == c->nlev - 1;
+  if constexpr (std::is_same<T, float>::value) whole = whole || (c->tail_l0 > 0 && l == c->tail_l0);
+  if (whole) {  // the coarsest solve, or the cluster tail from this level down
+    if (lp) {
+      GMG_CK(record_timing_event(E[0], s));
+      c->lev_kind[l] = 2;
+      c->lev_gs[l] = 0;
+    }
+    if (l == c->nlev - 1) GMG_TRY(launch_coarse<T>(c, b, x, s));
+    else GMG_TRY(launch_tail(c, s));
+    if (lp) {
+      GMG_CK(record_timing_event(E[5], s));
+      for (int k = l + 1; k < c->nlev; ++k) c->lev_kind[k] = 0;
+    }
+    return GMG_OK;
+  }
   Level& C = c->L[l + 1];
   const bool prof = c->prof && l == 0;
   if (prof) GMG_CK(record_timing_event(c->ev[0], s));
+  if (lp) GMG_CK(record_timing_event(E[0], s));
   int gs = 0;
   for (int it = 0; it < c->opt.nu_pre; ++it)
     for (int k = (it == 0 && c0_done) ? 1 : 0; k < L.ncolor; ++k, ++gs) GMG_TRY(launch_gs_colour<T>(L, k, b, x, s));
   if (prof) GMG_CK(record_timing_event(c->ev[1], s));
+  if (lp) GMG_CK(record_timing_event(E[1], s));
   GMG_TRY(launch_residual<T>(L, x, b, Vec<T>::r(L), s));
   const bool next_c0 = c->opt.nu_pre > 0 && l + 1 < c->nlev - 1;
   GMG_TRY(launch_restrict<T>(L, Vec<T>::r(L), Vec<T>::b(C), Vec<T>::x(C), s, next_c0 ? Vec<T>::dinv(C) : nullptr,
                              next_c0 ? C.color_off[1] : 0));
+  if (lp) GMG_CK(record_timing_event(E[2], s));
   GMG_TRY(vcycle<T>(c, l + 1, s, next_c0));
+  if (lp) GMG_CK(record_timing_event(E[3], s));
   GMG_TRY(launch_prolong<T>(L, Vec<T>::x(C), x, s));
   if (prof) GMG_CK(record_timing_event(c->ev[2], s));
+  if (lp) GMG_CK(record_timing_event(E[4], s));
   for (int it = 0; it < c->opt.nu_post; ++it)
     for (int q = 0; q < L.ncolor; ++q, ++gs) {
       const int k = c->opt.post_forward ? q : L.ncolor - 1 - q;
@@ -842,6 +880,11 @@ gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s, bool c0_done) {
   if (prof) {
     GMG_CK(record_timing_event(c->ev[3], s));
     c->prof_gs = gs;
+  }
+  if (lp) {
+    GMG_CK(record_timing_event(E[5], s));
+    c->lev_kind[l] = 1;
+    c->lev_gs[l] = gs;
   }
   return GMG_OK;
 }
@@ -857,8 +900,8 @@ template gmg_status launch_prolong<double>(Level&, const double*, double*, cudaS
 template gmg_status launch_prolong<float>(Level&, const float*, float*, cudaStream_t);
 template gmg_status launch_coarse<double>(gmg_ctx*, const double*, double*, cudaStream_t);
 template gmg_status launch_coarse<float>(gmg_ctx*, const float*, float*, cudaStream_t);
-template gmg_status vcycle<double>(gmg_ctx*, int, cudaStream_t, bool);
-template gmg_status vcycle<float>(gmg_ctx*, int, cudaStream_t, bool);
+template gmg_status vcycle<double>(gmg_ctx*, int, cudaStream_t, bool, double*, const double*);
+template gmg_status vcycle<float>(gmg_ctx*, int, cudaStream_t, bool, float*, const float*);
 
 gmg_status launch_gather(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t s) {
   return launch(k_gather, blocks_for(n), 256, s, n, perm, src, dst);
@@ -893,19 +936,27 @@ static gmg_status dot(gmg_ctx* c, int64_t n, const double* a, const double* b, i
   return launch(k_reduce_final, 1, 256, s, kRedBlocks, (const double*)c->red, c->scal + slot);
 }
 
-// A finest-level V-cycle, bracketed by timing events when profiling is on.
+// A finest-level V-cycle, bracketed by timing events when profiling is on;
+// x and b replace the finest level's own vectors when given.
 template <class T>
-static gmg_status timed_vcycle(gmg_ctx* c, cudaStream_t s, bool c0_done) {
+static gmg_status timed_vcycle(gmg_ctx* c, cudaStream_t s, bool c0_done, T* x = nullptr, const T* b = nullptr) {
   if (c->prof) GMG_CK(record_timing_event(c->ev[4], s));
-  GMG_TRY(vcycle<T>(c, 0, s, c0_done));
+  GMG_TRY(vcycle<T>(c, 0, s, c0_done, x, b));
   if (c->prof) GMG_CK(record_timing_event(c->ev[5], s));
   return GMG_OK;
 }
 
-// z = MGI32(0, r), widened to FP64.
-static gmg_status precond32(gmg_ctx* c, const double* r, double* z, cudaStream_t s) {
+static bool pcg_mode(int mode) { return mode == GMG_FP32_PCG || mode == GMG_FP64_PCG; }
+
+// z = MGI(0, r) in the mode's cycle precision (FP64: z itself is the cycle's
+// iterate; FP32: widened from the finest level's x32).
+static gmg_status precond(gmg_ctx* c, int mode, const double* r, double* z, cudaStream_t s) {
   Level& L = c->L[0];
   const int64_t n0 = c->opt.nu_pre > 0 ? L.color_off[1] : 0;
+  if (mode == GMG_FP64_PCG) {
+    GMG_TRY(launch(k_zero_c0, blocks_for(L.n), 256, s, L.n, r, z, (const double*)L.dinv64, n0));
+    return timed_vcycle<double>(c, s, n0 > 0, z, r);
+  }
   GMG_TRY(launch(k_d2f_zero, blocks_for(L.n), 256, s, L.n, r, L.b32, L.x32, (const float*)L.dinv32, n0));
   GMG_TRY(timed_vcycle<float>(c, s, n0 > 0));
   return launch_f2d(L.n, L.x32, z, s);
@@ -914,24 +965,25 @@ static gmg_status precond32(gmg_ctx* c, const double* r, double* z, cudaStream_t
 // One outer iteration (captured as a graph when enabled).
 //  FP64         : x <- MGI(x, b) (FP64 cycle on the iterate), r = b - A x, rr
 //  FP32_REFINE  : e = MGI32(0, r), x += e, r = b - A x, rr
-//  FP32_PCG seg 0: q = A p, pq, alpha = rz/pq, x += alpha p, r -= alpha q, rr
-//  FP32_PCG seg 1: z = MGI32(0, r), num = z.(r - r_old), rz' = r.z,
-//                  p = z + (num/rz) p, rz = rz'
+//  *_PCG seg 0  : q = A p, pq, alpha = rz/pq, x += alpha p, r -= alpha q, rr
+//  *_PCG seg 1  : z = MGI(0, r) (FP32 or FP64 cycle), num = z.(r - r_old),
+//                 rz' = r.z, p = z + (num/rz) p, rz = rz'
 gmg_status iteration_body(gmg_ctx* c, int mode, int seg, cudaStream_t s, cudaGraphConditionalHandle h, bool check) {
   Level& L = c->L[0];
   const int64_t n = L.n;
+  const int64_t n0 = c->opt.nu_pre > 0 ? L.color_off[1] : 0;
   if (mode == GMG_FP64) {
     GMG_TRY(timed_vcycle<double>(c, s, false));  // level-0 x64/b64 alias xs/bs
     return outer_residual(c, S_RR, s);
   }
   if (mode == GMG_FP32_REFINE) {
-    const int64_t n0 = c->opt.nu_pre > 0 ? L.color_off[1] : 0;
     GMG_TRY(launch(k_d2f_zero, blocks_for(n), 256, s, n, (const double*)c->rs, L.b32, L.x32, (const float*)L.dinv32,
                    n0));
     GMG_TRY(timed_vcycle<float>(c, s, n0 > 0));
     GMG_TRY(launch(k_add_f2d, blocks_for(n), 256, s, n, (const float*)L.x32, c->xs));
     return outer_residual(c, S_RR, s);
   }
+  const bool f64 = mode == GMG_FP64_PCG;
   if (seg == 0) {
     const int64_t nb = (L.A.nslice * 32 + 255) / 256;
     if (nb > c->red_cap) {
@@ -940,21 +992,32 @@ gmg_status iteration_body(gmg_ctx* c, int mode, int seg, cudaStream_t s, cudaGra
     }
     GMG_TRY(launch(k_spmv_dot, nb, 256, s, L.A.nslice, L.A.ptr, L.A.row0, L.A.nrow, L.A.col, L.A.v64, L.diag64,
                    (const double*)c->ps, c->qs, c->red, c->red_cnt, c->scal + S_PQ));
-    return launch(k_pcg_axpy, kRedBlocks, 256, s, n, c->scal, (const double*)c->ps, (const double*)c->qs, c->xs,
-                  c->rs, c->ros, L.b32, L.x32, (const float*)L.dinv32, c->opt.nu_pre > 0 ? L.color_off[1] : 0,
-                  c->red, c->red_cnt + 1, check ? 1 : 0, c->dloop, c->dhist, h);
+    if (f64)
+      return launch(k_pcg_axpy<double>, kRedBlocks, 256, s, n, c->scal, (const double*)c->ps, (const double*)c->qs,
+                    c->xs, c->rs, c->ros, (float*)nullptr, c->zs, (const double*)L.dinv64, n0, c->red,
+                    c->red_cnt + 1, check ? 1 : 0, c->dloop, c->dhist, h);
+    return launch(k_pcg_axpy<float>, kRedBlocks, 256, s, n, c->scal, (const double*)c->ps, (const double*)c->qs,
+                  c->xs, c->rs, c->ros, L.b32, L.x32, (const float*)L.dinv32, n0, c->red, c->red_cnt + 1,
+                  check ? 1 : 0, c->dloop, c->dhist, h);
   }
-  // b32 = r and x32 (colour 0 already smoothed from zero) were set by segment 0
-  GMG_TRY(timed_vcycle<float>(c, s, c->opt.nu_pre > 0));
-  GMG_TRY(launch(k_pcg_zdots, kRedBlocks, 256, s, n, (const float*)L.x32, (const double*)c->rs,
+  // the cycle's right-hand side and initial iterate (colour 0 already
+  // smoothed from zero) were set by segment 0
+  if (f64) {
+    GMG_TRY(timed_vcycle<double>(c, s, n0 > 0, c->zs, (const double*)c->rs));
+    GMG_TRY(launch(k_pcg_zdots<double>, kRedBlocks, 256, s, n, (const double*)c->zs, (const double*)c->rs,
+                   (const double*)c->ros, c->red, c->red_cnt + 2, c->scal));
+    return launch(k_pcg_dir<double>, blocks_for(n), 256, s, n, (const double*)c->scal, (const double*)c->zs, c->ps);
+  }
+  GMG_TRY(timed_vcycle<float>(c, s, n0 > 0));
+  GMG_TRY(launch(k_pcg_zdots<float>, kRedBlocks, 256, s, n, (const float*)L.x32, (const double*)c->rs,
                  (const double*)c->ros, c->red, c->red_cnt + 2, c->scal));
-  return launch(k_pcg_dir, blocks_for(n), 256, s, n, (const double*)c->scal, (const float*)L.x32, c->ps);
+  return launch(k_pcg_dir<float>, blocks_for(n), 256, s, n, (const double*)c->scal, (const float*)L.x32, c->ps);
 }
 
-// PCG start: z = MGI32(0, r), rz = r.z, p = z (r must be current).
-gmg_status pcg_start(gmg_ctx* c, cudaStream_t s) {
+// PCG start: z = MGI(0, r), rz = r.z, p = z (r must be current).
+gmg_status pcg_start(gmg_ctx* c, int mode, cudaStream_t s) {
   const int64_t n = c->L[0].n;
-  GMG_TRY(precond32(c, c->rs, c->zs, s));
+  GMG_TRY(precond(c, mode, c->rs, c->zs, s));
   GMG_TRY(dot(c, n, c->rs, c->zs, S_RZ, s));
   return launch(k_copy, blocks_for(n), 256, s, n, (const double*)c->zs, c->ps);
 }
@@ -968,7 +1031,7 @@ __global__ void k_iter_check(double* sc, int* it, double* hist, cudaGraphConditi
 }
 
 gmg_status loop_body(gmg_ctx* c, int mode, cudaGraphConditionalHandle h, cudaStream_t s) {
-  if (mode == GMG_FP32_PCG) {
+  if (pcg_mode(mode)) {
     GMG_TRY(iteration_body(c, mode, 1, s));
     return iteration_body(c, mode, 0, s, h, true);
   }

@@ -6,7 +6,8 @@
 namespace gmg {
 
 gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s);
-gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P, cudaStream_t s);
+gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P, const int32_t* const* coloring,
+                      cudaStream_t s);
 
 // level-vector selection by precision
 template <class T> struct Vec;
@@ -38,7 +39,10 @@ template <class T> gmg_status launch_restrict(Level& L, const T* r, T* bc, T* xc
                                               const T* dinvc = nullptr, int64_t nc0 = 0);
 template <class T> gmg_status launch_prolong(Level& L, const T* u, T* x, cudaStream_t s);
 template <class T> gmg_status launch_coarse(gmg_ctx* c, const T* b, T* x, cudaStream_t s);
-template <class T> gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s, bool c0_done = false);
+// MGI(x_l, b_l, l) on the level's own vectors, or on x_in / b_in (finest
+// level only) when given.
+template <class T> gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s, bool c0_done = false, T* x_in = nullptr,
+                                     const T* b_in = nullptr);
 
 gmg_status launch_d2f(int64_t n, const double* a, float* b, cudaStream_t s);
 gmg_status launch_f2d(int64_t n, const float* a, double* b, cudaStream_t s);
@@ -46,7 +50,7 @@ gmg_status launch_f2d(int64_t n, const float* a, double* b, cudaStream_t s);
 // the end of the iteration where the iteration's kernels allow it.
 gmg_status iteration_body(gmg_ctx* c, int mode, int seg, cudaStream_t s, cudaGraphConditionalHandle h = 0,
                           bool check = false);
-gmg_status pcg_start(gmg_ctx* c, cudaStream_t s);
+gmg_status pcg_start(gmg_ctx* c, int mode, cudaStream_t s);
 gmg_status outer_residual_norm(gmg_ctx* c, cudaStream_t s);
 gmg_status norm_b(gmg_ctx* c, cudaStream_t s);
 enum { S_NB2 = 0, S_RR = 1, S_RZ = 2, S_PQ = 3, S_NUM = 4, S_RZN = 5, S_BETA = 6, S_TOL = 7 };

@@ -273,10 +273,10 @@ struct gmg_ctx {
   uint64_t graph_kernels[8] = {};  // kernel nodes of each captured graph
   // device-side outer loop per mode: a graph whose conditional WHILE node
   // repeats the iteration until the convergence test fails on the device
-  cudaGraphExec_t loops[3] = {};
-  uint64_t loop_kernels[3] = {};  // kernel nodes of one loop iteration
-  bool loop_refused[3] = {};      // instantiation failed: the host loop serves the mode
-  bool loop_pdl[3] = {};          // the loop body kept its programmatic launch edges
+  cudaGraphExec_t loops[4] = {};
+  uint64_t loop_kernels[4] = {};  // kernel nodes of one loop iteration
+  bool loop_refused[4] = {};      // instantiation failed: the host loop serves the mode
+  bool loop_pdl[4] = {};          // the loop body kept its programmatic launch edges
   int* dloop = nullptr;           // device iteration counter, iteration limit
   double* dhist = nullptr;        // relative residual per iteration (max_iter + 1)
   cudaStream_t g_stream = nullptr;
@@ -288,6 +288,14 @@ struct gmg_ctx {
   cudaEvent_t ev[6] = {};
   double prof_acc[4] = {0, 0, 0, 0};  // smoothing ms, GS launches, cycle ms, cycles
   int prof_gs = 0;                    // finest-level GS launches of the last timed cycle
+  // per-level timing of the same cycles: six events per level (before and
+  // after pre-smoothing, after the restriction, after the coarser levels,
+  // after the prolongation, after post-smoothing); levels run inside the
+  // cluster tail or as the coarsest solve record only the first and last
+  std::vector<cudaEvent_t> lev_ev;
+  std::vector<int> lev_kind;    // per level: 0 not recorded, 1 all six events, 2 first and last only
+  std::vector<int> lev_gs;      // GS launches of the level in the last timed cycle
+  std::vector<double> lev_acc;  // per level: smoothing ms, GS launches, transfer ms, whole-level ms
 };
 
 namespace gmg {

@@ -83,7 +83,8 @@ using namespace gmg;
 extern "C" {
 
 gmg_status gmg_setup_ML(gmg_handle* h, const double* M_diag, const gmg_csr* L, double t, int n_prolong,
-                        const gmg_prolong* P, const gmg_options* opt, void* stream) {
+                        const gmg_prolong* P, const int32_t* const* coloring, const gmg_options* opt,
+                        void* stream) {
   if (!h || !M_diag || !L || !L->rowptr || !L->col || !L->val || L->n <= 0 || !(t >= 0.0)) {
     set_error("gmg_setup_ML: null pointer, n <= 0 or t < 0");
     return GMG_ERR_INVALID_ARG;
@@ -105,7 +106,7 @@ gmg_status gmg_setup_ML(gmg_handle* h, const double* M_diag, const gmg_csr* L, d
       return GMG_ERR_INVALID_ARG;
     }
   gmg_csr A = {n, L->rowptr, L->col, Aval.data()};
-  GMG_TRY(gmg_setup(h, &A, n_prolong, P, opt, stream));
+  GMG_TRY(gmg_setup(h, &A, n_prolong, P, coloring, opt, stream));
   gmg_ctx* c = *h;
   auto fail = [&](gmg_status st) {
     std::string keep = gmg_last_error();
@@ -185,3 +186,10 @@ gmg_status gmg_grad(gmg_handle h, const double* lambda, const double* x, double*
 }
 
 }  // extern "C"
+
+// The pattern gradient under the name of the interface it belongs to:
+// G_vals[k] = -lambda_i x_j on L's stored entries and dLdt = -lambda^T L x.
+extern "C" gmg_status gmg_grad_pattern(gmg_handle h, const double* lambda, const double* x, double* G_vals, double* dLdt,
+                            void* stream) {
+  return gmg_grad(h, lambda, x, nullptr, dLdt, G_vals, stream);
+}

@@ -80,11 +80,35 @@ __global__ void __launch_bounds__(256) k_noalloc_finish(int nblocks, const doubl
   }
 }
 
-// Device address of the partials array, looked up once per device (with
-// that device current) and cached.
+// Device address of the partials array, looked up once per device context
+// (with that device current) and cached.  The cache is keyed on the CUDA
+// context current at the call as well as the device index: after
+// cudaDeviceReset the device gets a new primary context in which the
+// library's module (and the array) is loaded again at a new address, so the
+// first call in the new context looks the address up afresh.
 constexpr int kMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static double* g_noalloc_ptr[kMaxDevices] = {};
+static void* g_noalloc_ctx[kMaxDevices] = {};
+
+// The current context through the driver's cuCtxGetCurrent, reached via the
+// runtime (the library does not link the driver library directly); NULL when
+// no context is current on the calling thread or the query is unavailable.
+static void* current_context() {
+  typedef int (*ctx_get_fn)(void**);
+  static ctx_get_fn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    const bool ok = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                        cudaSuccess &&
+                    q == cudaDriverEntryPointSuccess;
+    cudaGetLastError();
+    return ok ? (ctx_get_fn)f : (ctx_get_fn) nullptr;
+  }();
+  void* ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
 
 static gmg_status noalloc_scratch(double** out) {
   int dev = 0;
@@ -94,14 +118,18 @@ static gmg_status noalloc_scratch(double** out) {
     return GMG_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  void* ctx = current_context();
+  // Without a known context (none current yet, or the query is unavailable)
+  // the address is looked up on every call: still correct, only slower.
+  if (!ctx || !g_noalloc_ptr[dev] || g_noalloc_ctx[dev] != ctx) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);  // makes the primary context current
     if (e != cudaSuccess || !p) {
       set_error(std::string("gmg_residual_norm_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       return GMG_ERR_CUDA;
     }
     g_noalloc_ptr[dev] = (double*)p;
+    g_noalloc_ctx[dev] = current_context();
   }
   *out = g_noalloc_ptr[dev];
   return GMG_OK;

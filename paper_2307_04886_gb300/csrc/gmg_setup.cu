@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -853,14 +854,45 @@ static gmg_status upload_ell(Arena& a, Ell& E, const EllPlan& P, const std::vect
   return GMG_OK;
 }
 
-// Colours level l, renumbers it colour by colour (ascending caller index within
-// a colour), and builds the sliced-ELL layout of its off-diagonal part.
+// Checks a caller's colouring of a level with pattern (rp, ci): every colour in
+// [0, n) and no two adjacent rows of the same colour (rows of one colour must
+// be independent for the in-place Gauss-Seidel update).  Returns the number
+// of colours (largest + 1) or -1 after setting the error message.
+static int check_colouring(int l, int64_t n, const int64_t* rp, const int32_t* ci, const int32_t* color) {
+  int nc = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (color[i] < 0 || color[i] >= n) {
+      set_error("coloring[" + std::to_string(l) + "]: colour of row " + std::to_string(i) + " outside [0, n)");
+      return -1;
+    }
+    nc = std::max(nc, color[i] + 1);
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (ci[k] != i && color[ci[k]] == color[i]) {
+        set_error("coloring[" + std::to_string(l) + "]: adjacent rows " + std::to_string(i) + " and " +
+                  std::to_string(ci[k]) + " share colour " + std::to_string(color[i]));
+        return -1;
+      }
+  return nc;
+}
+
+// Colours level l (the caller's colouring when given, else greedy first fit),
+// renumbers it colour by colour (ascending caller index within a colour), and
+// builds the sliced-ELL layout of its off-diagonal part.
 static gmg_status build_level_structure(gmg_ctx* c, int l, const int64_t* rp, const int32_t* ci,
-                                        std::vector<int32_t>& perm, std::vector<int32_t>& iperm) {
+                                        const int32_t* given, std::vector<int32_t>& perm,
+                                        std::vector<int32_t>& iperm) {
   Level& L = c->L[l];
   const int64_t n = L.n;
   std::vector<int32_t> color;
-  L.ncolor = greedy_colour(n, rp, ci, color);
+  if (given) {
+    L.ncolor = check_colouring(l, n, rp, ci, given);
+    if (L.ncolor < 0) return GMG_ERR_INVALID_ARG;
+    color.assign(given, given + n);
+  } else {
+    L.ncolor = greedy_colour(n, rp, ci, color);
+  }
   L.h_color = color;
   L.color_off.assign(L.ncolor + 1, 0);
   for (int64_t i = 0; i < n; ++i) L.color_off[color[i] + 1]++;
@@ -1202,7 +1234,7 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s) {
 }
 
 // ---- validation (host) ----
-static gmg_status validate(const gmg_csr* A, int nP, const gmg_prolong* P) {
+static gmg_status validate(const gmg_csr* A, int nP, const gmg_prolong* P, const int32_t* const* coloring) {
   if (!A || A->n <= 0 || !A->rowptr || !A->col || !A->val) {
     set_error("A: null pointer or n <= 0");
     return GMG_ERR_INVALID_ARG;
@@ -1298,6 +1330,10 @@ static gmg_status validate(const gmg_csr* A, int nP, const gmg_prolong* P) {
     set_error("coarsest level has " + std::to_string(nf) + " rows (limit " + std::to_string(kMaxCoarse) + ")");
     return GMG_ERR_TOO_LARGE;
   }
+  // a caller colouring of level 0 is checked here, before any device work
+  // (the coarse levels' patterns are known only after the symbolic product)
+  if (coloring && coloring[0] && check_colouring(0, n, A->rowptr, A->col, coloring[0]) < 0)
+    return GMG_ERR_INVALID_ARG;
   return GMG_OK;
 }
 
@@ -1426,8 +1462,9 @@ static gmg_status build_tail(gmg_ctx* c) {
   return GMG_OK;
 }
 
-gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P, cudaStream_t s) {
-  GMG_TRY(validate(A, nP, P));
+gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P, const int32_t* const* coloring,
+                      cudaStream_t s) {
+  GMG_TRY(validate(A, nP, P, coloring));
   GMG_CK(cudaGetDevice(&c->device));
   Arena& a = c->arena;
   c->nlev = nP + 1;
@@ -1476,7 +1513,8 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   // colouring, renumbering, layouts
   std::vector<std::vector<int32_t>> perm(c->nlev), iperm(c->nlev);
   for (int l = 0; l < c->nlev; ++l)
-    GMG_TRY(build_level_structure(c, l, hrp[l].data(), hcol[l].data(), perm[l], iperm[l]));
+    GMG_TRY(build_level_structure(c, l, hrp[l].data(), hcol[l].data(), coloring ? coloring[l] : nullptr, perm[l],
+                                  iperm[l]));
   for (int l = 0; l + 1 < c->nlev; ++l)
     GMG_TRY(build_transfer_structure(c, l, P[l], perm[l], iperm[l], perm[l + 1], iperm[l + 1]));
   // coarsest dense buffers
@@ -1515,3 +1553,26 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
 }
 
 }  // namespace gmg
+
+namespace gmg {
+__global__ void k_pivot_reciprocal(int64_t n, const double* __restrict__ d, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = recip_newton(d[i]);
+}
+}  // namespace gmg
+
+// The reciprocal the coarsest inverse takes of every pivot, applied to n
+// device values (exposed so that its accuracy can be checked against the
+// correctly rounded FP64 division).
+extern "C" gmg_status gmg_pivot_reciprocal(int64_t n, const double* d, double* out, void* stream) {
+  using namespace gmg;
+  if (n < 0 || (n > 0 && (!d || !out))) {
+    set_error("gmg_pivot_reciprocal: negative size or null pointer");
+    return GMG_ERR_INVALID_ARG;
+  }
+  if (n == 0) return GMG_OK;
+  const int64_t grid = std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_pivot_reciprocal<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(n, d, out);
+  GMG_LAUNCHED();
+  return GMG_OK;
+}

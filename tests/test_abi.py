@@ -59,10 +59,10 @@ def test_null_arguments_are_rejected_without_touching_the_device(lib):
     import ctypes
 
     h = lib.load_library()
-    assert h.gmg_setup(None, None, 0, None, None, None) == lib.GMG_ERR_INVALID_ARG
+    assert h.gmg_setup(None, None, 0, None, None, None, None) == lib.GMG_ERR_INVALID_ARG
     assert h.gmg_solve(None, None, None, 1e-10, 0, None, None) == lib.GMG_ERR_INVALID_ARG
     assert h.gmg_solve_batched(None, 1, None, None, 1e-10, 0, None, None) == lib.GMG_ERR_INVALID_ARG
     assert h.gmg_destroy(None) == lib.GMG_OK
     hh = ctypes.c_void_p()
-    assert h.gmg_setup(ctypes.byref(hh), None, 0, None, None, None) == lib.GMG_ERR_INVALID_ARG
+    assert h.gmg_setup(ctypes.byref(hh), None, 0, None, None, None, None) == lib.GMG_ERR_INVALID_ARG
     assert b"A" in h.gmg_last_error()

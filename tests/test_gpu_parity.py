@@ -1,7 +1,9 @@
 """GPU parity: every step of Alg. 2, whole V-cycles and whole solves of the
 CUDA library against the CPU FP64 oracle, through the C ABI.
 
-Tolerances (normwise relative, ||gpu - oracle|| / ||oracle||):
+Every comparison asserts the tolerance both normwise,
+||gpu - oracle|| / ||oracle||, and element by element,
+max_i |gpu_i - oracle_i| <= tol * max_i |oracle_i| (parity_util.assert_close):
   * FP64 steps and FP64 V-cycles: 1e-12 (only the summation order, the
     reciprocal diagonal and the explicit coarse inverse differ);
   * FP32 steps and FP32 V-cycles: 1e-6 (inputs rounded to FP32, about
@@ -15,14 +17,11 @@ import pytest
 
 import gmg_inputs as gi
 import oracle
+from parity_util import assert_close as close
 
 pytestmark = pytest.mark.gpu
 
 SEED = 1234
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
 
 
 @pytest.fixture(scope="module")
@@ -83,21 +82,21 @@ def test_steps_match(pair, fp32, tol):
         for desc in (False, True):
             xo = o.smooth(l, x, b, 2, desc)
             xg = _np(g.smooth(l, _t(x), _t(b), 2, desc, fp32=fp32))
-            assert rel(xg, xo) <= tol, f"smooth level {l} desc={desc}"
+            close(xg, xo, tol, f"smooth level {l} desc={desc}")
         ro = o.residual(l, x, b)
         rg = _np(g.residual(l, _t(x), _t(b), _t(np.zeros(n)), fp32=fp32))
-        assert rel(rg, ro) <= tol * 10, f"residual level {l}"
+        close(rg, ro, tol * 10, f"residual level {l}")
         bo = o.restrict(l, b)
         bg = _np(g.restrict(l, _t(b), _t(np.zeros(nc)), fp32=fp32))
-        assert rel(bg, bo) <= tol, f"restrict level {l}"
+        close(bg, bo, tol, f"restrict level {l}")
         po = o.prolong_add(l, u, x)
         pg = _np(g.prolong_add(l, _t(u), _t(x), fp32=fp32))
-        assert rel(pg, po) <= tol, f"prolong level {l}"
+        close(pg, po, tol, f"prolong level {l}")
     nl = o.n(o.nlev - 1)
     b = rng.standard_normal(nl)
     co = o.coarse_solve(b)
     cg = _np(g.coarse_solve(_t(b), _t(np.zeros(nl)), fp32=fp32))
-    assert rel(cg, co) <= max(tol, 1e-11), "coarse solve"
+    close(cg, co, max(tol, 1e-11), "coarse solve")
 
 
 @pytest.mark.parametrize("fp32,tol", [(False, 1e-12), (True, 1e-6)])
@@ -108,18 +107,21 @@ def test_vcycle_matches(pair, fp32, tol):
     b = s.b
     xo = o.vcycle(x0, b)
     xg = _np(g.vcycle(_t(x0), _t(b), fp32=fp32))
-    assert rel(xg, xo) <= tol
+    close(xg, xo, tol, "first V-cycle")
     # a second cycle from the first one's output
     xo2 = o.vcycle(xo, b)
     xg2 = _np(g.vcycle(_t(xg), _t(b), fp32=fp32))
-    assert rel(xg2, xo2) <= tol
+    close(xg2, xo2, tol, "second V-cycle")
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_solve_matches(gmg, precision):
+    """Solves to 1e-10 in every precision mode.  The FP64 modes (the
+    stationary iteration of Alg. 1 and CG preconditioned by the FP64 cycle)
+    take the oracle's iteration count with the same residual history."""
     s = gi.icosphere_system(5)
     o = oracle.Oracle(s.A, s.Ps)
-    xo, ito, ho, ok = o.solve(s.b, tol=1e-10, pcg=precision == 2)
+    xo, ito, ho, ok = o.solve(s.b, tol=1e-10, pcg=precision in (2, 3))
     assert ok
     g = gmg.Solver(s.A, s.Ps, precision=precision)
     xg, it, rr, hist, st = g.solve(_t(s.b), tol=1e-10, history=101)
@@ -127,8 +129,8 @@ def test_solve_matches(gmg, precision):
     true_rel = np.linalg.norm(s.b - s.A @ xg) / np.linalg.norm(s.b)
     assert true_rel <= 1e-10
     assert abs(true_rel - rr) <= 1e-12
-    assert rel(xg, xo) <= 1e-8
-    if precision == 0:
+    close(xg, xo, 1e-8, "solution")
+    if precision in (0, 3):
         assert it == ito
         assert np.allclose(hist, ho, rtol=1e-6, atol=0)
     else:
@@ -176,7 +178,7 @@ def test_single_level_is_direct_solve(gmg):
     assert it == 1 and rr <= 1e-12
     import scipy.sparse.linalg as sla
 
-    assert rel(_np(x), sla.spsolve(s.A.tocsc(), s.b)) <= 1e-12
+    close(_np(x), sla.spsolve(s.A.tocsc(), s.b), 1e-12, "direct solve")
     g.close()
 
 
@@ -191,7 +193,7 @@ def test_set_values_refresh(gmg):
     g.set_values(A3.data)
     o = oracle.Oracle(A3, s.Ps)
     for l in range(o.nlev):
-        assert rel(g.level(l)[0].data, o.level(l)[0].data) <= 1e-13
+        close(g.level(l)[0].data, o.level(l)[0].data, 1e-13, f"refreshed level {l}")
     x, it, rr, _, _ = g.solve(_t(s.b), tol=1e-10)
     assert np.linalg.norm(s.b - A3 @ _np(x)) / np.linalg.norm(s.b) <= 1e-10
     g.close()
@@ -209,7 +211,7 @@ def test_batched_matches_single(gmg):
             r = np.linalg.norm(B[:, c] - s.A @ X[:, c]) / np.linalg.norm(B[:, c])
             assert r <= 1e-10
             xs = _np(g.solve(_t(B[:, c].copy()), tol=1e-10)[0])
-            assert rel(X[:, c], xs) <= 1e-8
+            close(X[:, c], xs, 1e-8, f"batched column {c}")
         g.close()
 
 
@@ -224,10 +226,14 @@ def test_full_size_torus(gmg):
         Ao, co = o.level(l)
         Ag, cg = g.level(l)
         assert np.array_equal(Ao.indices, Ag.indices) and np.array_equal(co, cg)
-        assert rel(Ag.data, Ao.data) <= 1e-13
+        assert np.array_equal(Ag.data, Ao.data), f"Galerkin level {l}"
     xo = o.vcycle(np.zeros(s.n), s.b)
-    xg = _np(g.vcycle(_t(np.zeros(s.n)), _t(s.b), fp32=True))
-    assert rel(xg, xo) <= 1e-6
+    close(_np(g.vcycle(_t(np.zeros(s.n)), _t(s.b), fp32=True)), xo, 1e-6, "FP32 V-cycle, full size")
+    close(_np(g.vcycle(_t(np.zeros(s.n)), _t(s.b), fp32=False)), xo, 1e-12, "FP64 V-cycle, full size")
+    rng = np.random.default_rng(SEED + 11)
+    x0 = rng.standard_normal(s.n)
+    xo = o.vcycle(x0, s.b)
+    close(_np(g.vcycle(_t(x0), _t(s.b), fp32=True)), xo, 1e-6, "FP32 V-cycle from a random iterate, full size")
     x, it, rr, _, _ = g.solve(_t(s.b), tol=1e-10)
     assert np.linalg.norm(s.b - s.A @ _np(x)) / np.linalg.norm(s.b) <= 1e-10
     g.close()
@@ -245,8 +251,8 @@ def test_fixed_warp_split_matches(gmg, split):
     x0 = rng.standard_normal(s.n)
     g.set_lanes([split] * (g.nlev - 1))
     xo = o.vcycle(x0, s.b)
-    assert rel(_np(g.vcycle(_t(x0), _t(s.b), fp32=False)), xo) <= 1e-12
-    assert rel(_np(g.vcycle(_t(x0), _t(s.b), fp32=True)), xo) <= 1e-6
+    close(_np(g.vcycle(_t(x0), _t(s.b), fp32=False)), xo, 1e-12, f"FP64 cycle, split {split}")
+    close(_np(g.vcycle(_t(x0), _t(s.b), fp32=True)), xo, 1e-6, f"FP32 cycle, split {split}")
     with pytest.raises(gmg.GMGError):
         g.set_lanes([3] * (g.nlev - 1))
     x, _, _, _, _ = g.solve(_t(s.b), tol=1e-10)
@@ -277,7 +283,7 @@ def test_coarsest_inverse_sizes(gmg, n):
     x, it, rr, _, st = g.solve(_t(b), tol=1e-10)
     assert st == 0 and it == 1
     xe = np.linalg.solve(A.toarray(), b)
-    assert rel(_np(x), xe) <= 1e-12 * max(1.0, np.linalg.cond(A.toarray()) / 100)
+    close(_np(x), xe, 1e-12 * max(1.0, np.linalg.cond(A.toarray()) / 100), f"coarsest solve n={n}")
     g.close()
 
 
@@ -299,7 +305,7 @@ def test_coarsest_not_positive_definite_is_reported(gmg):
     assert e.value.status == gmg.GMG_ERR_CHOLESKY
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_device_loop_matches_host_loop(gmg, precision):
     """The outer iterations run in a device-side graph loop (conditional WHILE
     node) unless per-cycle timing is on, which uses the host-driven loop: both
@@ -346,9 +352,162 @@ def test_tail_cluster_matches_kernel_per_phase_path(gmg, monkeypatch):
         k0 = gmg.kernel_launches()
         xg = _np(g.vcycle(_t(x0), _t(s.b), fp32=True))
         res[tail] = (xg, gmg.kernel_launches() - k0)
-        assert rel(xg, xo) <= 1e-6
+        close(xg, xo, 1e-6, f"FP32 cycle, tail={tail}")
         x, it, rr, _, st = g.solve(_t(s.b), tol=1e-10)
         assert st == 0 and np.linalg.norm(s.b - s.A @ _np(x)) <= 1e-10 * np.linalg.norm(s.b)
         g.close()
     assert res[True][1] < res[False][1]
-    assert rel(res[True][0], res[False][0]) <= 1e-6
+    close(res[True][0], res[False][0], 1e-6, "tail vs per-phase kernels")
+
+
+@pytest.mark.parametrize("tail", [True, False])
+def test_ragged_colour_slices(gmg, monkeypatch, tail):
+    """A torus (250 x 122, 3 levels) on which the last 32-row slice of EVERY
+    colour of every smoothed level is partial, so each colour launch ends in a
+    padded slice: the steps and whole cycles match the oracle element by
+    element, with the FP32 cycle's last levels in the cluster tail or as one
+    kernel per phase."""
+    if tail:
+        monkeypatch.delenv("GMG_NO_TAIL", raising=False)
+    else:
+        monkeypatch.setenv("GMG_NO_TAIL", "1")
+    s = gi.torus_system(250, 122, 1e-4, 11)
+    o = oracle.Oracle(s.A, s.Ps)
+    for l in range(o.nlev - 1):
+        counts = np.bincount(o.level(l)[1])
+        assert np.all(counts % 32 != 0), f"level {l}: a colour fills whole slices ({counts})"
+    g = gmg.Solver(s.A, s.Ps, precision=gmg.GMG_FP32_PCG)
+    rng = np.random.default_rng(SEED + 21)
+    for l in range(o.nlev - 1):
+        n = o.n(l)
+        x, b = rng.standard_normal(n), rng.standard_normal(n)
+        for fp32, tol in ((False, 1e-12), (True, 1e-6)):
+            close(_np(g.smooth(l, _t(x), _t(b), 2, False, fp32=fp32)), o.smooth(l, x, b, 2, False), tol,
+                  f"ragged smooth level {l} fp32={fp32}")
+            close(_np(g.residual(l, _t(x), _t(b), _t(np.zeros(n)), fp32=fp32)), o.residual(l, x, b), tol * 10,
+                  f"ragged residual level {l} fp32={fp32}")
+    x0 = rng.standard_normal(s.n)
+    xo = o.vcycle(x0, s.b)
+    close(_np(g.vcycle(_t(x0), _t(s.b), fp32=False)), xo, 1e-12, "ragged FP64 cycle")
+    close(_np(g.vcycle(_t(x0), _t(s.b), fp32=True)), xo, 1e-6, "ragged FP32 cycle")
+    x, it, rr, _, st = g.solve(_t(s.b), tol=1e-10)
+    assert st == 0 and np.linalg.norm(s.b - s.A @ _np(x)) <= 1e-10 * np.linalg.norm(s.b)
+    g.close()
+
+
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 8, 13, 16])
+def test_batched_vcycle_matches_oracle_per_column(gmg, nrhs):
+    """One FP32 multi-right-hand-side V-cycle (the SpMM-style kernels of the
+    batched and many-mesh solves, column blocks of 1, 2, 4, 8 and 16 with zero
+    padding for 3 and 13) against the oracle's cycle, column by column, on a
+    ragged torus; a second cycle from the first one's output."""
+    s = gi.torus_system(250, 122, 1e-4, 11)
+    o = oracle.Oracle(s.A, s.Ps)
+    g = gmg.Solver(s.A, s.Ps)
+    rng = np.random.default_rng(SEED + 30 + nrhs)
+    X0 = rng.standard_normal((s.n, nrhs))
+    B = rng.standard_normal((s.n, nrhs)) * s.Mdiag[:, None]
+    X1 = _np(g.vcycle_batched(_t(X0), _t(B)))
+    X2 = _np(g.vcycle_batched(_t(X1), _t(B)))
+    for c in range(nrhs):
+        xo1 = o.vcycle(X0[:, c], B[:, c])
+        close(X1[:, c], xo1, 1e-6, f"batched cycle column {c} of {nrhs}")
+        close(X2[:, c], o.vcycle(xo1, B[:, c]), 1e-6, f"second batched cycle column {c} of {nrhs}")
+    g.close()
+
+
+def test_many_meshes_one_iteration_matches_oracle(gmg):
+    """One outer iteration of the many-mesh solve (max_iter = 1) from random
+    initial iterates: X1 = X0 + MGI32(0, B - A X0) per mesh and column, which
+    equals the oracle's MGI(X0, B) up to the FP32 cycle's rounding (the cycle
+    is affine in its iterate)."""
+    systems = gi.spheres_batch(count=4, lo=800, hi=6000, nrhs=3, seed=8, stop=200)
+    many = gmg.SolverMany([(s.A, s.Ps) for s in systems], max_iter=1)
+    rng = np.random.default_rng(SEED + 40)
+    X0 = [rng.standard_normal((s.n, 3)) for s in systems]
+    Xs, its, rels, st = many.solve([_t(s.b) for s in systems], [_t(x) for x in X0], tol=1e-30,
+                                   raise_on_fail=False)
+    assert st == gmg.GMG_ERR_NOT_CONVERGED and all(i == 1 for i in its)
+    for s, x0, X in zip(systems, X0, Xs):
+        o = oracle.Oracle(s.A, s.Ps)
+        Xn = _np(X)
+        for c in range(3):
+            close(Xn[:, c], o.vcycle(x0[:, c], s.b[:, c]), 1e-6, f"mesh n={s.n} column {c}")
+    many.close()
+
+
+def test_pivot_reciprocal_within_one_ulp(gmg):
+    """The Newton-Raphson reciprocal used for every pivot of the coarsest
+    inverse against the correctly rounded division 1.0 / d: a log-spaced sweep
+    over [1e-30, 1e30], values next to powers of two and the FP32-range edges
+    (where the FP64 division takes over) stay within one unit in the last
+    place."""
+    import torch
+
+    d = np.concatenate([
+        np.logspace(-30, 30, 20001),
+        np.ldexp(1.0, np.arange(-99, 100)) * (1 + 2.0**-52),
+        np.ldexp(1.0, np.arange(-99, 100)) * (1 - 2.0**-53),
+        np.random.default_rng(5).uniform(0.5, 2.0, 20000),
+        np.array([1e-30, 1e30, 9.99e-31, 1.001e30, 3.0, 7.0, 1.0 / 3.0, np.pi]),
+    ])
+    dd = torch.tensor(d, device="cuda")
+    out = torch.empty_like(dd)
+    lib = gmg.load_library()
+    import ctypes
+
+    st = lib.gmg_pivot_reciprocal(d.size, ctypes.c_void_p(dd.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == gmg.GMG_OK
+    r = _np(out)
+    exact = 1.0 / d
+    ulps = np.abs(r - exact) / np.spacing(exact)
+    assert ulps.max() <= 1.0, f"worst {ulps.max()} ulp at d = {d[ulps.argmax()]!r}"
+
+
+def _reverse_greedy(A):
+    n = A.shape[0]
+    col = -np.ones(n, np.int64)
+    for i in range(n - 1, -1, -1):
+        used = {col[j] for j in A.indices[A.indptr[i]:A.indptr[i + 1]] if j != i and col[j] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        col[i] = c
+    return col.astype(np.int32)
+
+
+def test_caller_colouring_matches_oracle_with_it(gmg):
+    """gmg_setup with a caller colouring on every level (greedy first fit in
+    decreasing row index, unlike the default) against the oracle built with
+    the same colouring: identical colourings, bitwise Galerkin levels, FP64 and
+    FP32 cycles element by element, a solve to 1e-10.  A colouring that is
+    improper on a coarse level (checked after the symbolic product) is
+    refused."""
+    s = gi.torus_system(250, 122, 1e-4, 11)
+    o0 = oracle.Oracle(s.A, s.Ps)
+    given = [_reverse_greedy(o0.level(l)[0]) for l in range(o0.nlev)]
+    o = oracle.Oracle(s.A, s.Ps, coloring=given)
+    g = gmg.Solver(s.A, s.Ps, precision=gmg.GMG_FP32_PCG, coloring=given)
+    for l in range(o.nlev):
+        Ao, co = o.level(l)
+        Ag, cg = g.level(l)
+        assert np.array_equal(cg, given[l]) and np.array_equal(co, cg)
+        assert np.array_equal(Ag.data, Ao.data)
+    rng = np.random.default_rng(SEED + 50)
+    x0 = rng.standard_normal(s.n)
+    xo = o.vcycle(x0, s.b)
+    close(_np(g.vcycle(_t(x0), _t(s.b), fp32=False)), xo, 1e-12, "FP64 cycle, caller colouring")
+    close(_np(g.vcycle(_t(x0), _t(s.b), fp32=True)), xo, 1e-6, "FP32 cycle, caller colouring")
+    x, it, rr, _, st = g.solve(_t(s.b), tol=1e-10)
+    assert st == 0 and np.linalg.norm(s.b - s.A @ _np(x)) <= 1e-10 * np.linalg.norm(s.b)
+    g.close()
+    bad = list(given)
+    A1 = o0.level(1)[0]
+    c1 = given[1].copy()
+    j = next(j for j in A1.indices[A1.indptr[0]:A1.indptr[1]] if j != 0)
+    c1[j] = c1[0]
+    bad[1] = c1
+    with pytest.raises(gmg.GMGError) as e:
+        gmg.Solver(s.A, s.Ps, coloring=bad)
+    assert e.value.status == gmg.GMG_ERR_INVALID_ARG

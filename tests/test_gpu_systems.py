@@ -3,13 +3,17 @@ Sec. 5.2 with eta = 1e-6 (nearly singular) and the bi-Laplacian smoothing of
 Sec. 5.5 (two-ring stencil, wider Galerkin rows, more colours).
 
 Tolerances: Galerkin levels and colourings bit-exact.  One V-cycle against
-the oracle (normwise relative): the coarse solves differ in rounding (explicit
+the oracle (normwise and element-wise relative to the largest entry): the coarse solves differ in rounding (explicit
 inverse vs Cholesky), which the coarsest operator amplifies by its condition
 number kappa, so the bound is max(1e-12, 10 kappa 2^-53) in FP64 and
 max(1e-6, 10 kappa 2^-24) in FP32 (1e-12 and 1e-6 for the bi-Laplacian,
 kappa = 3.9).  The Poisson coarsest operator has kappa = 3.2e8: its FP64 bound
 is 3.5e-7, and an FP32 cycle carries no accuracy in the near-constant mode
 (kappa 2^-24 > 1), so only its use as a preconditioner is tested (the solves).
+The FP32 bound also scales with the stencil (fp32_stencil_factor): the
+bi-Laplacian's 19-entry rows carry off-diagonal mass up to 5.5 times their
+diagonal, so one FP32 Gauss-Seidel update may round about 7.5 times more than
+on the 7-entry Laplace-type rows for which 1e-6 is stated.
 Solves reach the stated residual in every precision.  The Poisson system
 stalls near a 1e-8 relative residual in FP64 (a direct solve's own residual is
 2.5e-8 on this mesh), so it is solved to 1e-7, still above the paper's 1e-4,
@@ -20,6 +24,7 @@ import scipy.sparse.linalg as sla
 
 import gmg_inputs as gi
 import oracle
+from parity_util import assert_close as close
 
 pytestmark = pytest.mark.gpu
 
@@ -38,8 +43,18 @@ def _t(x):
     return torch.tensor(np.asarray(x, dtype=np.float64), device="cuda")
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+def fp32_stencil_factor(A):
+    """How much larger the worst-case FP32 rounding of one Gauss-Seidel update,
+    n eps sum_j |a_ij x_j| / |a_ii x_i|, is on this operator than on the
+    Laplace-type rows (7 entries, off-diagonal mass at most twice the
+    diagonal) that the 1e-6 FP32 tolerance was stated for: (z_max
+    gamma_max) / (7 * 2), with z_max the longest row and gamma_max the largest
+    sum_j |a_ij| / a_ii.  About 7.5 for the bi-Laplacian's 19-entry two-ring
+    rows, 1 for Laplace-type systems."""
+    d = A.diagonal()
+    gamma = (abs(A) @ np.ones(A.shape[0])) / d
+    zmax = int(np.diff(A.indptr).max())
+    return max(1.0, zmax * float(gamma.max()) / (7 * 2.0))
 
 
 @pytest.fixture(scope="module", params=["poisson", "bilaplacian"])
@@ -65,9 +80,10 @@ def test_levels_and_cycles_match(gmg, system):
     rng = np.random.default_rng(21)
     x0 = rng.standard_normal(s.n)
     xo = o.vcycle(x0, s.b)
-    assert rel(g.vcycle(_t(x0), _t(s.b), fp32=False).cpu().numpy(), xo) <= max(1e-12, 10 * kappa * 2.0**-53)
+    close(g.vcycle(_t(x0), _t(s.b), fp32=False).cpu().numpy(), xo, max(1e-12, 10 * kappa * 2.0**-53), "FP64 cycle")
     if kappa * 2.0**-24 < 1e-3:
-        assert rel(g.vcycle(_t(x0), _t(s.b), fp32=True).cpu().numpy(), xo) <= max(1e-6, 10 * kappa * 2.0**-24)
+        close(g.vcycle(_t(x0), _t(s.b), fp32=True).cpu().numpy(), xo,
+              max(1e-6 * fp32_stencil_factor(s.A), 10 * kappa * 2.0**-24), "FP32 cycle")
     g.close()
 
 
@@ -80,5 +96,5 @@ def test_solves(gmg, system, precision):
     assert st == 0
     assert np.linalg.norm(s.b - s.A @ xn) <= tol * np.linalg.norm(s.b)
     xe = sla.spsolve(s.A.tocsc(), s.b)
-    assert rel(xn, xe) <= (1e-6 if name == "poisson" else 1e-8)
+    close(xn, xe, 1e-6 if name == "poisson" else 1e-8, "solution vs direct solve")
     g.close()

@@ -24,8 +24,9 @@ def g():
     return g
 
 
-def _setup(g, A, Ps=()):
-    """Calls gmg_setup through the C ABI; returns (status, last error)."""
+def _setup(g, A, Ps=(), colour0=None):
+    """Calls gmg_setup through the C ABI (with a caller colouring of level 0
+    when given); returns (status, last error)."""
     lib = g.load_library()
     A = sp.csr_matrix(A)
     rp = np.ascontiguousarray(A.indptr, dtype=np.int64)
@@ -39,8 +40,13 @@ def _setup(g, A, Ps=()):
         w = np.ascontiguousarray(w, dtype=np.float64)
         keep += [idx, w]
         arr[l] = g.gmg_prolong(nf, nc, idx.ctypes.data, w.ctypes.data)
+    coloring = None
+    if colour0 is not None:
+        c0 = np.ascontiguousarray(colour0, dtype=np.int32)
+        keep.append(c0)
+        coloring = (ctypes.c_void_p * (len(Ps) + 1))(c0.ctypes.data)
     h = ctypes.c_void_p()
-    st = lib.gmg_setup(ctypes.byref(h), ctypes.byref(csr), len(Ps), arr, None, None)
+    st = lib.gmg_setup(ctypes.byref(h), ctypes.byref(csr), len(Ps), arr, coloring, None, None)
     assert not h.value  # nothing is handed out on failure
     return st, lib.gmg_last_error().decode()
 
@@ -129,3 +135,20 @@ def test_coarsest_level_above_the_dense_limit(g):
     the 8,192-row limit of the coarsest level."""
     st, msg = _setup(g, _lap1d(8193))
     assert st == g.GMG_ERR_TOO_LARGE and "8192" in msg
+
+
+def test_improper_caller_colouring_rejected(g):
+    """A caller colouring of level 0 in which two adjacent rows share a colour
+    (their Gauss-Seidel updates would race) or a colour lies outside [0, n)
+    is rejected before any device work."""
+    n = 10
+    A = _lap1d(n)
+    even_odd = np.arange(n) % 2  # proper for the path graph
+    bad = even_odd.copy()
+    bad[4] = bad[3]  # rows 3 and 4 are adjacent
+    st, msg = _setup(g, A, colour0=bad)
+    assert st == g.GMG_ERR_INVALID_ARG and "share colour" in msg
+    neg = even_odd.copy()
+    neg[2] = -1
+    st, msg = _setup(g, A, colour0=neg)
+    assert st == g.GMG_ERR_INVALID_ARG and "outside" in msg

@@ -5,8 +5,10 @@ or an allocation would synchronise the device); this entry point serves them
 with a static device scratch array instead of library allocations.  Its
 result must agree with the library's regular residual entry point
 (gmg_residual on the finest level, FP64) within the FP64 step tolerance of
-the parity tests (1e-12 normwise), on two calls in a row, and repeated calls
-must give identical bits.  This file is collected last so that a run stopping
+the parity tests (1e-12, normwise and element-wise), on two calls in a row,
+and repeated calls must give identical bits.  The residual and both norms
+are also checked against the CPU oracle's residual (the plain row-by-row
+definition r = b - A x in FP64).  This file is collected last so that a run stopping
 at its first failure has already run every other test.
 """
 import ctypes
@@ -15,6 +17,8 @@ import numpy as np
 import pytest
 
 import gmg_inputs as gi
+import oracle
+from parity_util import assert_close as close
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +43,8 @@ def test_noalloc_residual_matches_regular_entry_point(cuda):
     r_ref = solver.residual(0, x.clone(), b.clone(), torch.zeros_like(b))
     torch.cuda.synchronize()
     norms_ref = np.array([torch.linalg.norm(r_ref).item(), torch.linalg.norm(b).item()])
+    r_oracle = oracle.Oracle(A, s.Ps).residual(0, x.cpu().numpy(), s.b)
+    norms_oracle = np.array([np.linalg.norm(r_oracle), np.linalg.norm(s.b)])
 
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     outs = []
@@ -53,8 +59,10 @@ def test_noalloc_residual_matches_regular_entry_point(cuda):
         torch.cuda.synchronize()
         rn, nn = r.cpu().numpy(), norms.cpu().numpy()
         rr = r_ref.cpu().numpy()
-        assert np.linalg.norm(rn - rr) <= 1e-12 * np.linalg.norm(rr)
+        close(rn, rr, 1e-12, "against gmg_residual")
         assert np.all(np.abs(nn - norms_ref) <= 1e-12 * norms_ref)
+        close(rn, r_oracle, 1e-12, "against the oracle's residual")
+        assert np.all(np.abs(nn - norms_oracle) <= 1e-12 * norms_oracle)
         outs.append((rn, nn))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     solver.close()
