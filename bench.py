@@ -15,7 +15,14 @@ starts; L2 is flushed (256 MB write) before every timed step.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmg|reference]
 
 With --impl reference the CPU FP64 oracle is timed on the same workload (one
-full setup + solve per step, on the host cores).
+full setup + solve per step, on all host cores).
+
+Beside the headline the JSON line carries, under config.workloads, the other
+synthetic workloads measured on the same GPU (--configs none skips them):
+icosphere5 (plain FP64 V-cycle iteration), heat512k (forward + adjoint solve of
+the differentiable heat diffusion), spheres64 (64 meshes x 8 right-hand sides
+in one many-mesh solve against 512 plain FP64 single solves) and cloud4m (the
+4M-point kNN cloud, with Gauss-Seidel GB/s per level).
 """
 from __future__ import annotations
 
@@ -145,6 +152,49 @@ def gs_launch_bytes(dims, s):
     return sweep / C
 
 
+def gs_level_launch_bytes(dims, l, s):
+    """Average algorithmic bytes of one Gauss-Seidel colour launch on level l
+    (the formula of gs_launch_bytes on that level's rows, entries, colours)."""
+    n, z, C = dims[l]
+    return ((z - n) * (s + 4) + 3 * n * s + (C - 1) * n * s) / C
+
+
+def level_breakdown(dims, lanes, levels, cycles, s=4):
+    """Per smoothed level of the timed cycles: Gauss-Seidel launches, average
+    launch time and algorithmic GB/s, the transfer (residual, restriction,
+    prolongation) time, and the cluster tail (levels it covers, time)."""
+    out, tail = [], None
+    cyc = max(cycles, 1)
+    for l, (gs_ms, gs_n, tr_ms, whole_ms) in enumerate(levels):
+        if l >= len(dims) - 1:
+            break
+        if gs_n > 0:
+            us = 1e3 * gs_ms / gs_n
+            b = gs_level_launch_bytes(dims, l, s)
+            out.append({"level": l, "rows": dims[l][0], "colours": dims[l][2], "kernel": f"k_gs<float, {lanes[l]}>",
+                        "gs_launches_per_cycle": gs_n / cyc, "gs_us_per_launch": us,
+                        "gs_bytes_per_launch": b, "gs_gbs": b / (us * 1e-6) / 1e9,
+                        "gs_us_per_cycle": 1e3 * gs_ms / cyc, "transfer_us_per_cycle": 1e3 * tr_ms / cyc})
+        elif whole_ms > 0 and tail is None:
+            tail = {"kernel": "k_tail_cycle", "levels": list(range(l, len(dims))), "us_per_cycle": 1e3 * whole_ms / cyc}
+    return out, tail
+
+
+def dominant_gs(per_level):
+    """The Gauss-Seidel kernel instantiation with the largest time per cycle,
+    summed over the levels that run it: (name, us per launch, bytes per launch,
+    us per cycle)."""
+    groups = {}
+    for r in per_level:
+        g = groups.setdefault(r["kernel"], [0.0, 0.0, 0.0, []])
+        g[0] += r["gs_us_per_cycle"]
+        g[1] += r["gs_launches_per_cycle"]
+        g[2] += r["gs_bytes_per_launch"] * r["gs_launches_per_cycle"]
+        g[3].append(r["level"])
+    name, (us_cyc, n_cyc, bytes_cyc, lv) = max(groups.items(), key=lambda kv: kv[1][0])
+    return name, us_cyc / n_cyc, bytes_cyc / n_cyc, us_cyc, lv
+
+
 def ncu_traffic(kernel, workload):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
     of `kernel` on `workload` from the committed ncu capture summary, or None."""
@@ -165,35 +215,58 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def oracle_step(s, lib_path=None):
+    """One oracle step on system s: the full setup of Alg. 1 (Galerkin levels,
+    colourings, Cholesky) and the V-cycle-preconditioned CG solve to 1e-10.
+    Returns (setup ms, solve ms, iterations)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    o = oracle.Oracle(s.A, s.Ps, lib_path=lib_path)
+    t1 = time.perf_counter()
+    x, iters, hist, ok = o.solve(s.b, tol=1e-10, max_iter=200, pcg=True)
+    t2 = time.perf_counter()
+    del o
+    return (t1 - t0) * 1e3, (t2 - t1) * 1e3, iters
+
+
+def threaded_oracle():
+    """(library path, cores) of the all-cores oracle build, or (None, 1)."""
+    import oracle
+
+    path = oracle.compile_oracle_threaded()
+    return (path, oracle.host_cores()) if path else (None, 1)
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    import numpy as np
-
     import gmg_inputs as gi
     import oracle
 
     oracle.compile_oracle()
+    path, cores = threaded_oracle()
     s = gi.workload(WORKLOAD)
-    times, iters = [], 0
+    times, setups, solves, iters = [], [], [], 0
     for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        o = oracle.Oracle(s.A, s.Ps)
-        x, iters, hist, ok = o.solve(s.b, tol=1e-10, max_iter=200, pcg=True)
-        dt = (time.perf_counter() - t0) * 1e3
-        del o
+        su, so, iters = oracle_step(s, path)
         if k >= args.warmup:
-            times.append(dt)
+            times.append(su + so)
+            setups.append(su)
+            solves.append(so)
     ms = sum(times) / len(times)
     line = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "solver": "CPU FP64 oracle: Galerkin setup + Cholesky + V-cycle-preconditioned CG",
-                   "iterations": iters},
-        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full oracle runs (setup + {iters} PCG iterations to 1e-10)"},
+        "config": {"workload": WORKLOAD_DESC,
+                   "solver": "CPU FP64 oracle: Galerkin setup + colouring + Cholesky + V-cycle-preconditioned CG",
+                   "iterations": iters, "setup_ms": sum(setups) / len(setups),
+                   "solve_ms": sum(solves) / len(solves)},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full oracle runs (setup + {iters} PCG iterations to 1e-10) on "
+                                   f"{cores} host threads (OpenMP over independent rows)"},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -201,16 +274,167 @@ def run_reference(args):
 
 
 def cpu_baseline(s):
+    """The oracle on the same system: all host cores (the threaded build) and
+    one thread (the paper's setting), one full step each."""
     import oracle
 
     oracle.compile_oracle()
-    t0 = time.perf_counter()
-    o = oracle.Oracle(s.A, s.Ps)
-    x, iters, hist, ok = o.solve(s.b, tol=1e-10, max_iter=200, pcg=True)
-    ms = (time.perf_counter() - t0) * 1e3
-    return {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"one full oracle run on the same system: Galerkin setup + Cholesky + {iters} FP64 "
-                      f"V-cycle-preconditioned CG iterations to 1e-10, single thread"}
+    path, cores = threaded_oracle()
+    su1, so1, it1 = oracle_step(s)
+    out = {"unit": "ms", "kind": "oracle",
+           "single_thread": {"value": su1 + so1, "setup_ms": su1, "solve_ms": so1, "cores": 1}}
+    if path:
+        su, so, it = oracle_step(s, path)
+        out.update(value=su + so, cores=cores, setup_ms=su, solve_ms=so,
+                   sample=f"one full oracle step on the same system (Galerkin setup + colouring + Cholesky + {it} "
+                          f"FP64 V-cycle-preconditioned CG iterations to 1e-10) on {cores} host threads; "
+                          f"single_thread: the same step on one thread")
+    else:
+        out.update(value=su1 + so1, cores=1,
+                   sample=f"one full oracle step on one thread ({it1} PCG iterations); no OpenMP runtime")
+    return out
+
+
+def _ev_ms(fn, reps):
+    """Average ms of fn() over reps runs, timed with CUDA events on the current stream."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def other_workloads(g, names, steps):
+    """Timings of the other synthetic workloads (each inputs-resident, events
+    on the solve stream); a workload that cannot be set up is reported with
+    its error."""
+    import numpy as np
+    import torch
+
+    import gmg_inputs as gi
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    res = {}
+    for name in names:
+        t0 = time.perf_counter()
+        try:
+            if name == "icosphere5":
+                s = gi.workload(name)
+                b = torch.tensor(s.b, device=dev)
+                x = torch.zeros_like(b)
+                r = {"rows": s.n}
+                for tag, prec in (("fp64_plain", g.GMG_FP64), ("fp32_pcg", g.GMG_FP32_PCG)):
+                    sv = g.Solver(s.A, s.Ps, precision=prec)
+                    sv.autotune()
+                    out = {}
+
+                    def run():
+                        x.zero_()
+                        out["r"] = sv.solve(b, x, tol=1e-10)
+
+                    _ev_ms(run, 3)
+                    r[f"{tag}_ms"] = _ev_ms(run, steps)
+                    r[f"{tag}_iterations"] = out["r"][1]
+                    sv.close()
+                res[name] = r
+            elif name == "heat512k":
+                s = gi.workload(name)
+                sv = g.Solver(None, s.Ps, precision=g.GMG_FP32_PCG, ml=(s.Mdiag, s.L, s.t))
+                sv.autotune()
+                u0 = torch.tensor(s.extra["u0"], device=dev)
+                xt = torch.tensor(s.extra["x_target"], device=dev)
+                x, lam = torch.zeros_like(u0), torch.zeros_like(u0)
+                it = {}
+
+                def fwd_adj():
+                    sv.set_t(s.t)
+                    bb = sv.mass(u0)
+                    x.zero_()
+                    it["f"] = sv.solve(bb, x, tol=1e-10)[1]
+                    lam.zero_()
+                    it["a"] = sv.solve(2.0 * (x - xt), lam, tol=1e-10)[1]
+                    sv.grad(lam, x)
+
+                _ev_ms(fwd_adj, 2)
+                res[name] = {"rows": s.n, "forward_adjoint_ms": _ev_ms(fwd_adj, steps),
+                             "step": "set_t (numeric refresh) + M u0 + forward solve + adjoint solve + gradient kernel",
+                             "forward_iterations": it["f"], "adjoint_iterations": it["a"], "tol": 1e-10}
+                sv.close()
+            elif name == "spheres64":
+                systems = gi.cached_batch("spheres64", gi.spheres_batch)
+                many = g.SolverMany([(q.A, q.Ps) for q in systems])
+                Bs = [torch.tensor(q.b, device=dev) for q in systems]
+                Xs = [torch.zeros_like(B) for B in Bs]
+                out = {}
+
+                def run_many():
+                    for X in Xs:
+                        X.zero_()
+                    out["m"] = many.solve(Bs, Xs, tol=1e-10)
+
+                _ev_ms(run_many, 2)
+                many_ms = _ev_ms(run_many, steps)
+                its = out["m"][1]
+                many.close()
+                singles = [g.Solver(q.A, q.Ps, precision=g.GMG_FP64) for q in systems]
+                cols = [[B[:, c].contiguous() for c in range(B.shape[1])] for B in Bs]
+                xs = [torch.zeros_like(cs[0]) for cs in cols]
+
+                def run_single():
+                    for sv, cs, xx in zip(singles, cols, xs):
+                        for bcol in cs:
+                            xx.zero_()
+                            sv.solve(bcol, xx, tol=1e-10)
+
+                run_single()
+                single_ms = _ev_ms(run_single, max(1, steps // 4))
+                for sv in singles:
+                    sv.close()
+                res[name] = {"meshes": len(systems), "rows_total": int(sum(q.n for q in systems)),
+                             "rhs_per_mesh": int(systems[0].b.shape[1]), "many_ms": many_ms,
+                             "many_iterations_max": int(max(its)), "many_iterations_min": int(min(its)),
+                             "plain_fp64_single_solves_ms": single_ms,
+                             "speedup_vs_plain_fp64": single_ms / many_ms,
+                             "plain": "every column solved alone by the plain FP64 V-cycle iteration (gmg_solve)"}
+            elif name == "cloud4m":
+                s = gi.workload(name)
+                sv = g.Solver(s.A, s.Ps, precision=g.GMG_FP32_PCG)
+                lanes = sv.autotune()
+                b = torch.tensor(s.b, device=dev)
+                x = torch.zeros_like(b)
+                out = {}
+
+                def run():
+                    x.zero_()
+                    out["r"] = sv.solve(b, x, tol=1e-10)
+
+                _ev_ms(run, 2)
+                ms = _ev_ms(run, steps)
+                sv.profile(True)
+                sv.profile_read()
+                sv.profile_levels()
+                for _ in range(2):
+                    run()
+                pr = sv.profile_read()
+                lv = sv.profile_levels()
+                sv.profile(False)
+                per_level, tail = level_breakdown(sv.dims, lanes, lv, int(pr[3]))
+                res[name] = {"rows": s.n, "levels": [d[0] for d in sv.dims], "nnz": [d[1] for d in sv.dims],
+                             "colours": [d[2] for d in sv.dims], "fp32_pcg_ms": ms, "iterations": out["r"][1],
+                             "vcycle_us_fp32": 1e3 * pr[2] / max(pr[3], 1),
+                             "vcycle_gbs_fp32": algorithmic_bytes(sv.dims, s.Ps, 4) / (pr[2] / max(pr[3], 1) * 1e-3) / 1e9,
+                             "per_level": per_level, "tail": tail}
+                sv.close()
+        except Exception as e:  # reported, not fatal: the headline stands on its own
+            res[name] = {"error": f"{type(e).__name__}: {e}"}
+        res.setdefault(name, {})["wall_s"] = time.perf_counter() - t0
+        torch.cuda.synchronize()
+    return res
 
 
 def main():
@@ -220,6 +444,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gmg", choices=["gmg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--configs", default="icosphere5,heat512k,spheres64,cloud4m",
+                    help="comma-separated other workloads to time after the headline, or 'none'")
     ap.add_argument("--profile-step", action="store_true",
                     help="set up, autotune, run `warmup` untimed steps and one step, print a short note and exit "
                          "(the launch sequence a kernel profiler lists; no timing is reported)")
@@ -282,6 +508,7 @@ def main():
         if prof:
             sv.profile(True)
             sv.profile_read()
+            sv.profile_levels()
         l0 = g.kernel_launches()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         torch.cuda.synchronize()
@@ -296,9 +523,10 @@ def main():
         launches = g.kernel_launches() - l0
         ms = [a.elapsed_time(bb) for a, bb in evs]
         pr = sv.profile_read() if prof else None
+        lv = sv.profile_levels() if prof else None
         if prof:
             sv.profile(False)
-        return sum(ms) / steps, iters, rr, launches, pr, wall
+        return sum(ms) / steps, iters, rr, launches, (pr, lv), wall
 
     if args.profile_step:
         for _ in range(args.warmup + 1):
@@ -313,29 +541,24 @@ def main():
     clk.start()
     ms, iters, rr, launches, _, wall = timed(solver, args.steps, args.warmup, prof=False, clk=clk)
     clocks = clk.stop()
-    # per-kernel timing (CUDA events around the finest smoothing blocks and each
-    # V-cycle) runs the host-driven loop: event nodes cannot sit in the device loop
-    _, _, _, _, pr, _ = timed(solver, 5, 1, prof=True)
+    # per-kernel timing (CUDA events around every level's smoothing blocks and
+    # each V-cycle) runs the host-driven loop: event nodes cannot sit in the device loop
+    _, _, _, _, (pr, lv), _ = timed(solver, 5, 1, prof=True)
     ms = max_over_ranks(ms, dev)
 
     # breakdown (not part of the headline): numeric setup alone
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(5):
-        solver.set_values(vals)
-    e1.record()
-    torch.cuda.synchronize()
-    setup_ms = e0.elapsed_time(e1) / 5
+    setup_ms = _ev_ms(lambda: solver.set_values(vals), 5)
 
-    # the plain FP64 V-cycle and FP32-cycle iterative refinement on the same hierarchy
+    # the plain FP64 V-cycle, FP32-cycle iterative refinement and CG with the
+    # FP64 cycle, on the same hierarchy
     others = {}
-    for name, prec in (("fp64_plain", g.GMG_FP64), ("fp32_refine", g.GMG_FP32_REFINE)):
+    for name, prec in (("fp64_plain", g.GMG_FP64), ("fp32_refine", g.GMG_FP32_REFINE), ("fp64_pcg", g.GMG_FP64_PCG)):
         sv = g.Solver(A, s.Ps, precision=prec)
         sv.set_lanes(lanes)
         o_ms, o_it, _, _, _, _ = timed(sv, max(2, args.steps // 2), 3)
-        _, _, _, _, o_pr, _ = timed(sv, 3, 1, prof=True)
-        others[name] = (o_ms, o_it, o_pr)
+        _, _, _, _, (o_pr, o_lv), _ = timed(sv, 3, 1, prof=True)
+        others[name] = (o_ms, o_it, o_pr, o_lv)
         sv.close()
 
     # end to end through the C ABI with host buffers (pinned), copies inside
@@ -353,19 +576,32 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
 
-    # roofline of the dominant kernel: finest-level FP32 Gauss-Seidel colour launch
+    # roofline: the Gauss-Seidel kernel instantiation with the largest share of
+    # the V-cycle (per-level CUDA events), and the whole V-cycle in each precision
     peak, peak_kind = load_peaks()
     smooth_ms, gs_launches, cyc_ms, cycles = pr
-    gs_avg_ms = smooth_ms / max(gs_launches, 1)
-    gs_bytes = gs_launch_bytes(dims, 4)
-    achieved = gs_bytes / (gs_avg_ms * 1e-3) / 1e9
+    cycles = int(cycles)
+    per_level, tail = level_breakdown(dims, lanes, lv, cycles)
+    kname, k_us, k_bytes, k_us_cyc, k_levels = dominant_gs(per_level)
+    achieved = k_bytes / (k_us * 1e-6) / 1e9
+    vc_us32 = 1e3 * cyc_ms / max(cycles, 1)
     vc_bytes32 = algorithmic_bytes(dims, s.Ps, 4)
-    vc_gbs = vc_bytes32 / (cyc_ms / max(cycles, 1) * 1e-3) / 1e9
+    vc_gbs32 = vc_bytes32 / (vc_us32 * 1e-6) / 1e9
     vc_bytes64 = algorithmic_bytes(dims, s.Ps, 8)
-    f_ms, f_it, f_pr = others["fp64_plain"]
-    r_ms, r_it, r_pr = others["fp32_refine"]
-    vc64_us = 1e3 * f_pr[2] / max(f_pr[3], 1)
-    traffic = ncu_traffic(f"k_gs<float, {lanes[0]}>", WORKLOAD)
+    f_ms, f_it, f_pr, f_lv = others["fp64_plain"]
+    r_ms, r_it, r_pr, r_lv = others["fp32_refine"]
+    p_ms, p_it, p_pr, p_lv = others["fp64_pcg"]
+    vc_us64 = 1e3 * f_pr[2] / max(f_pr[3], 1)
+    vc_gbs64 = vc_bytes64 / (vc_us64 * 1e-6) / 1e9
+    per_level64, _ = level_breakdown(dims, lanes, f_lv, int(f_pr[3]), s=8)
+    for r in per_level64:
+        r["kernel"] = r["kernel"].replace("float", "double")
+    traffic = ncu_traffic(kname, WORKLOAD)
+
+    extra = {}
+    names = [] if args.configs == "none" else [c for c in args.configs.split(",") if c]
+    if names and rank == 0:
+        extra = other_workloads(g, names, max(3, args.steps // 3))
 
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -383,16 +619,24 @@ def main():
             "numeric_setup_ms": setup_ms, "solve_ms": ms - setup_ms, "symbolic_setup_ms": symbolic_ms,
             "fp64_plain_ms": f_ms, "fp64_plain_iterations": f_it,
             "fp32_refine_ms": r_ms, "fp32_refine_iterations": r_it,
+            "fp64_pcg_ms": p_ms, "fp64_pcg_iterations": p_it,
             "speedup_vs_fp64_plain": f_ms / ms,
-            "vcycle_us_fp32": 1e3 * cyc_ms / max(cycles, 1), "vcycle_gbs_fp32": vc_gbs,
-            "vcycle_bytes_fp32": vc_bytes32, "vcycle_us_fp64": vc64_us,
-            "vcycle_gbs_fp64": vc_bytes64 / (vc64_us * 1e-6) / 1e9, "vcycle_bytes_fp64": vc_bytes64,
+            "speedup_fp32_cycle_inside_cg": p_ms / ms,
+            "speedup_cg_with_fp64_cycle_vs_fp64_plain": f_ms / p_ms,
+            "vcycle_us_fp32": vc_us32, "vcycle_gbs_fp32": vc_gbs32,
+            "vcycle_bytes_fp32": vc_bytes32, "vcycle_us_fp64": vc_us64,
+            "vcycle_gbs_fp64": vc_gbs64, "vcycle_bytes_fp64": vc_bytes64,
+            "per_level_fp32": per_level, "tail_fp32": tail, "per_level_fp64": per_level64,
             "wall_ms_timed_region": wall,
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+            "workloads": extra,
         },
-        "roofline": {"bound": "hbm", "kernel": f"k_gs<float, {lanes[0]}> (finest level, one colour)", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_kind": peak_kind, "bytes_per_launch": gs_bytes, "avg_launch_us": gs_avg_ms * 1e3},
+        "roofline": {"bound": "hbm", "kernel": f"{kname} (levels {k_levels}, one colour per launch)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind, "bytes_per_launch": k_bytes,
+                     "avg_launch_us": k_us, "us_per_vcycle": k_us_cyc, "share_of_vcycle": k_us_cyc / vc_us32,
+                     "vcycle_fp32": {"achieved": vc_gbs32, "frac": vc_gbs32 / peak, "us": vc_us32},
+                     "vcycle_fp64": {"achieved": vc_gbs64, "frac": vc_gbs64 / peak, "us": vc_us64}},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(A.data.nbytes + s.b.nbytes),
                 "d2h_bytes_per_step": int(8 * n)},
         "gpu_launches": int(launches),
