@@ -19,8 +19,10 @@
  * Readings of the paper that this file fixes:
  *   - the post-relaxation starts from y + P_l u, where y is the pre-relaxed
  *     iterate (the paper prints x + P_l u in Alg. 2);
- *   - relaxation is multicolour Gauss-Seidel: colours from a greedy first-fit
- *     colouring in increasing row index; pre-relaxation visits colours in
+ *   - relaxation is multicolour Gauss-Seidel: each level's colouring is the
+ *     one with fewer colours of two greedy first-fit colourings (increasing
+ *     row index; smallest-last order), each improved by iterated-greedy
+ *     passes, unless the caller gives one; pre-relaxation visits colours in
  *     ascending order, post-relaxation in descending order (a symmetric cycle),
  *     or ascending when `post_forward` is set;
  *   - the Galerkin product adds its terms (P_iJ P_jK) A_ij in a fixed order,
@@ -91,26 +93,110 @@ static void color_classes(olevel *L) {
   free(fill);
 }
 
-/* Greedy first-fit colouring in increasing row index: row i takes the smallest
- * colour not used by an already coloured neighbour (j < i). */
-static void greedy_color(olevel *L) {
+/* First fit along `order`: each row in turn takes the smallest colour that no
+ * neighbour coloured before it in this pass has.  Returns the colour count. */
+static int first_fit(const olevel *L, const int32_t *order, int32_t *color) {
   int64_t n = L->n;
-  int32_t *mark = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(n + 1));
-  for (int64_t c = 0; c <= n; ++c) mark[c] = -1;
-  L->color = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);
+  int64_t *seen = (int64_t *)xmalloc(sizeof(int64_t) * (size_t)(n + 1));
+  for (int64_t c = 0; c <= n; ++c) seen[c] = -1;
+  for (int64_t i = 0; i < n; ++i) color[i] = -1;
   int ncolor = 0;
-  for (int64_t i = 0; i < n; ++i) {
+  for (int64_t step = 0; step < n; ++step) {
+    int32_t i = order[step];
     for (int64_t k = L->rowptr[i]; k < L->rowptr[i + 1]; ++k) {
       int32_t j = L->col[k];
-      if (j < i) mark[L->color[j]] = (int32_t)i;
+      if (j != i && color[j] >= 0) seen[color[j]] = step;
     }
     int32_t c = 0;
-    while (mark[c] == (int32_t)i) ++c;
-    L->color[i] = c;
+    while (seen[c] == step) ++c;
+    color[i] = c;
     if (c + 1 > ncolor) ncolor = c + 1;
   }
-  free(mark);
-  L->ncolor = ncolor;
+  free(seen);
+  return ncolor;
+}
+
+/* Iterated greedy (Culberson): visit the colour classes from the highest
+ * colour to colour 0, rows in increasing index inside a class, and colour
+ * them again by first fit.  The count never grows. */
+static int recolour(const olevel *L, int ncolor, int32_t *color) {
+  int64_t n = L->n;
+  int32_t *order = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);
+  int64_t pos = 0;
+  for (int c = ncolor - 1; c >= 0; --c)
+    for (int64_t i = 0; i < n; ++i)
+      if (color[i] == c) order[pos++] = (int32_t)i;
+  int nc = first_fit(L, order, color);
+  free(order);
+  return nc;
+}
+
+/* Smallest-last order (Matula-Beck): repeatedly take out a row with the
+ * fewest neighbours still present and list the rows in reverse order of
+ * removal.  Rows with the same count form a stack: the initial stacks hold
+ * the rows with the smallest index on top, a row whose count drops is put on
+ * top of its new stack (neighbours handled in pattern order), and the row
+ * taken out is the top of the lowest non-empty stack. */
+static void smallest_last_order(const olevel *L, int32_t *order) {
+  int64_t n = L->n;
+  int32_t *cnt = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);
+  int32_t *up = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);   /* toward the top */
+  int32_t *down = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n); /* toward the bottom */
+  char *out = (char *)calloc((size_t)n, 1);
+  int maxc = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int c = 0;
+    for (int64_t k = L->rowptr[i]; k < L->rowptr[i + 1]; ++k)
+      if (L->col[k] != i) ++c;
+    cnt[i] = c;
+    if (c > maxc) maxc = c;
+  }
+  int32_t *top = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(maxc + 1));
+  for (int c = 0; c <= maxc; ++c) top[c] = -1;
+#define OR_PUT(v, c) do { down[v] = top[c]; up[v] = -1; if (top[c] >= 0) up[top[c]] = (v); top[c] = (v); } while (0)
+#define OR_TAKE(v, c) do { if (up[v] >= 0) down[up[v]] = down[v]; else top[c] = down[v]; \
+                           if (down[v] >= 0) up[down[v]] = up[v]; } while (0)
+  for (int64_t i = n - 1; i >= 0; --i) OR_PUT((int32_t)i, cnt[i]);
+  int low = 0;
+  for (int64_t left = n; left > 0; --left) {
+    if (low > 0) --low; /* one removal lowers the minimum count by at most one */
+    while (top[low] < 0) ++low;
+    int32_t v = top[low];
+    OR_TAKE(v, low);
+    out[v] = 1;
+    order[left - 1] = v;
+    for (int64_t k = L->rowptr[v]; k < L->rowptr[v + 1]; ++k) {
+      int32_t u = L->col[k];
+      if (u == v || out[u]) continue;
+      OR_TAKE(u, cnt[u]);
+      cnt[u] -= 1;
+      OR_PUT(u, cnt[u]);
+    }
+  }
+#undef OR_PUT
+#undef OR_TAKE
+  free(cnt); free(up); free(down); free(out); free(top);
+}
+
+#define OR_RECOLOUR_PASSES 8
+
+/* The colouring of a level: first fit in increasing row index and first fit
+ * in smallest-last order, each followed by OR_RECOLOUR_PASSES iterated-greedy
+ * passes; the one with fewer colours is kept (the first on a tie). */
+static void greedy_color(olevel *L) {
+  int64_t n = L->n;
+  int32_t *order = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);
+  int32_t *ca = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);
+  int32_t *cb = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) order[i] = (int32_t)i;
+  int na = first_fit(L, order, ca);
+  for (int p = 0; p < OR_RECOLOUR_PASSES; ++p) na = recolour(L, na, ca);
+  smallest_last_order(L, order);
+  int nb = first_fit(L, order, cb);
+  for (int p = 0; p < OR_RECOLOUR_PASSES; ++p) nb = recolour(L, nb, cb);
+  if (nb < na) { L->color = cb; L->ncolor = nb; free(ca); }
+  else { L->color = ca; L->ncolor = na; free(cb); }
+  free(order);
   color_classes(L);
 }
 

@@ -4,7 +4,8 @@
 //    (per-row hash sets in shared memory: count, scan, sorted fill) and a
 //    numeric pass with a fixed accumulation order, then mirrored to exact
 //    symmetry (the entry below the diagonal takes the value above it);
-//  * greedy colouring and colour-major renumbering (host, integer work);
+//  * colouring (two greedy colourings improved by iterated greedy, the one
+//    with fewer colours kept) and colour-major renumbering (host, integer work);
 //  * sliced-ELL layout of every level and of every restriction P_l^T;
 //  * explicit FP64 inverse of the coarsest level (the direct solve of
 //    Alg. 2 at the coarsest level) by block sweeps.
@@ -798,20 +799,110 @@ static gmg_status upload(Arena& a, T** d, const T* h, size_t n) {
   return GMG_OK;
 }
 
-// Greedy first-fit colouring in increasing row index over the pattern.
-static int greedy_colour(int64_t n, const int64_t* rp, const int32_t* ci, std::vector<int32_t>& color) {
-  color.assign(n, 0);
+// ---- colouring of a level's pattern (host).  Two greedy colourings are
+// built and the one with fewer colours kept (the first on a tie): first fit
+// in increasing row index, and first fit in smallest-last order (Matula and
+// Beck); each is then improved by kColourPasses passes of iterated greedy
+// (Culberson), which recolour by first fit visiting the colour classes from
+// the highest colour down, rows ascending within a class, and never add a
+// colour.  Every rule is deterministic, so the oracle, which implements the
+// same steps on its own, produces the same colouring.
+
+constexpr int kColourPasses = 8;
+
+// First fit in the given visiting order: each row takes the smallest colour
+// not used by a neighbour coloured earlier in this pass.
+static int first_fit(int64_t n, const int64_t* rp, const int32_t* ci, const std::vector<int32_t>& order,
+                     std::vector<int32_t>& color) {
+  color.assign(n, -1);
   std::vector<int64_t> mark(n + 1, -1);
   int ncol = 0;
-  for (int64_t i = 0; i < n; ++i) {
-    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
-      if (ci[k] < i) mark[color[ci[k]]] = i;
+  for (int64_t t = 0; t < n; ++t) {
+    const int32_t i = order[t];
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      const int32_t j = ci[k];
+      if (j != i && color[j] >= 0) mark[color[j]] = t;
+    }
     int32_t c = 0;
-    while (mark[c] == i) ++c;
+    while (mark[c] == t) ++c;
     color[i] = c;
     ncol = std::max(ncol, c + 1);
   }
   return ncol;
+}
+
+// One iterated-greedy pass: first fit over the classes of `color` from the
+// highest colour down, rows ascending within a class.
+static int iterated_pass(int64_t n, const int64_t* rp, const int32_t* ci, int ncol, std::vector<int32_t>& color) {
+  std::vector<int64_t> start(ncol + 1, 0);
+  for (int64_t i = 0; i < n; ++i) start[ncol - color[i]]++;  // class of colour c goes to slot ncol - 1 - c
+  for (int c = 0; c < ncol; ++c) start[c + 1] += start[c];
+  std::vector<int32_t> order(n);
+  for (int64_t i = 0; i < n; ++i) order[start[ncol - 1 - color[i]]++] = (int32_t)i;
+  return first_fit(n, rp, ci, order, color);
+}
+
+// Smallest-last order: rows sit in buckets by their number of neighbours not
+// yet removed, each bucket a stack (initially filled from the highest row
+// index down, so the smallest index is on top); the next row removed is the
+// top of the lowest non-empty bucket, and each of its remaining neighbours
+// (in pattern order) moves to the top of the bucket one lower.  The order is
+// the reverse of the removal order.
+static void smallest_last(int64_t n, const int64_t* rp, const int32_t* ci, std::vector<int32_t>& order) {
+  std::vector<int32_t> deg(n), next(n), prev(n);
+  int maxd = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int d = 0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) d += ci[k] != i;
+    deg[i] = d;
+    maxd = std::max(maxd, d);
+  }
+  std::vector<int32_t> head(maxd + 1, -1);
+  std::vector<char> gone(n, 0);
+  auto push = [&](int32_t v, int d) {
+    next[v] = head[d];
+    prev[v] = -1;
+    if (head[d] >= 0) prev[head[d]] = v;
+    head[d] = v;
+  };
+  auto unlink = [&](int32_t v, int d) {
+    if (prev[v] >= 0) next[prev[v]] = next[v];
+    else head[d] = next[v];
+    if (next[v] >= 0) prev[next[v]] = prev[v];
+  };
+  for (int64_t i = n - 1; i >= 0; --i) push((int32_t)i, deg[i]);
+  order.assign(n, 0);
+  int cur = 0;
+  for (int64_t t = n - 1; t >= 0; --t) {
+    cur = std::max(cur - 1, 0);
+    while (head[cur] < 0) ++cur;
+    const int32_t v = head[cur];
+    unlink(v, cur);
+    gone[v] = 1;
+    order[t] = v;
+    for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
+      const int32_t u = ci[k];
+      if (u == v || gone[u]) continue;
+      unlink(u, deg[u]);
+      --deg[u];
+      push(u, deg[u]);
+    }
+  }
+}
+
+static int greedy_colour(int64_t n, const int64_t* rp, const int32_t* ci, std::vector<int32_t>& color) {
+  std::vector<int32_t> order(n), other;
+  for (int64_t i = 0; i < n; ++i) order[i] = (int32_t)i;
+  int na = first_fit(n, rp, ci, order, color);
+  for (int p = 0; p < kColourPasses; ++p) na = iterated_pass(n, rp, ci, na, color);
+  smallest_last(n, rp, ci, order);
+  int nb = first_fit(n, rp, ci, order, other);
+  for (int p = 0; p < kColourPasses; ++p) nb = iterated_pass(n, rp, ci, nb, other);
+  if (nb < na) {
+    color.swap(other);
+    return nb;
+  }
+  return na;
 }
 
 // Sliced-ELL structure for `nrows` rows given the rows' entry lists; slices
@@ -877,7 +968,7 @@ static int check_colouring(int l, int64_t n, const int64_t* rp, const int32_t* c
   return nc;
 }
 
-// Colours level l (the caller's colouring when given, else greedy first fit),
+// Colours level l (the caller's colouring when given, else greedy_colour),
 // renumbers it colour by colour (ascending caller index within a colour), and
 // builds the sliced-ELL layout of its off-diagonal part.
 static gmg_status build_level_structure(gmg_ctx* c, int l, const int64_t* rp, const int32_t* ci,

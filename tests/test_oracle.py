@@ -5,7 +5,8 @@ iterate in the coarse correction, the wrong sweep order) fails one of them.
 
   Galerkin product  dense P^T A P (numpy), exact symmetry, constant mode
   Cholesky          L L^T = A, LAPACK's factor, solve residual
-  colouring         proper colouring + the first-fit characterisation
+  colouring         proper, complete (first fit: every smaller colour among the
+                    neighbours), never more colours than plain first fit
   Gauss-Seidel      matrix-splitting form (D + L_pi)^-1 (b - U_pi x)
   transfers         b - A x, P^T r, x + P u with scipy sparse products
   V-cycle           P = I is exact in one cycle; MGI(x, b) = x + B (b - A x)
@@ -108,20 +109,41 @@ def test_cholesky_of_coarsest(ico4):
     assert np.linalg.norm(Cd @ x - b) <= 1e-13 * np.linalg.norm(b)
 
 
+def _first_fit_count(A):
+    """Colours of the textbook greedy colouring in increasing row index."""
+    n = A.shape[0]
+    col = -np.ones(n, np.int64)
+    for i in range(n):
+        used = {col[j] for j in A.indices[A.indptr[i]:A.indptr[i + 1]] if j != i and col[j] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        col[i] = c
+    return int(col.max()) + 1
+
+
 @pytest.mark.parametrize("fx", ["ico4", "torus_small"])
-def test_greedy_colouring(fx, request):
+def test_colouring(fx, request):
+    """Every level's colouring is proper (rows of a colour are independent, so
+    the in-place multicolour sweep is a Gauss-Seidel sweep), complete (it is
+    the output of a first-fit pass: each row sees every smaller colour among
+    its neighbours), uses colours 0..C-1, and has no more colours than plain
+    first fit in increasing row index."""
     s, o = request.getfixturevalue(fx)
+    fewer = 0
     for l in range(o.nlev):
         A, col = o.level(l)
         rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
         off = rows != A.indices
         assert np.all(col[rows[off]] != col[A.indices[off]]), "adjacent rows share a colour"
-        # first fit in increasing row index: every smaller colour is used by a
-        # lower-index neighbour (this characterises the greedy colouring)
         for i in range(A.shape[0]):
             nb = A.indices[A.indptr[i]:A.indptr[i + 1]]
-            lower = set(col[nb[nb < i]].tolist())
-            assert set(range(col[i])) <= lower
+            assert set(range(col[i])) <= set(col[nb[nb != i]].tolist()), f"row {i} of level {l} is not first fit"
+        assert set(np.unique(col).tolist()) == set(range(o.dims[l][2]))
+        ff = _first_fit_count(A)
+        assert o.dims[l][2] <= ff
+        fewer += o.dims[l][2] < ff
+    assert fewer >= 1, "the iterated colouring should beat plain first fit somewhere"
 
 
 def _gs_splitting(A, col, x, b, descending):
