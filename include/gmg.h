@@ -208,24 +208,83 @@ gmg_status gmg_grad(gmg_handle h, const double *lambda, const double *x, double 
 gmg_status gmg_grad_pattern(gmg_handle h, const double *lambda, const double *x, double *G_vals, double *dLdt,
                             void *stream);
 
+/* ---- Sec. 4 hierarchy construction on the GPU ----
+ * Builds the prolongations P_l that gmg_setup takes, from the finest level's
+ * points and neighbour graph, level after level while a level has more than
+ * `stop` points (and at most max_levels levels; a level that does not shrink
+ * ends the hierarchy):
+ *   Sec. 4.2 sampling: points swept in index order; an eligible point becomes
+ *            a sample and makes every point within Dijkstra distance r
+ *            (Euclidean edge lengths, inside the sample's 2-ring) ineligible;
+ *            r = phi^(-1/3) times the mean edge length (summed per row, per
+ *            block of 1024 rows, then over blocks, each in index order);
+ *   Sec. 4.3 graph Voronoi cells of the samples (multi-source shortest paths,
+ *            ties to the smaller sample index) and the coarse neighbour graph
+ *            of cells that share an edge;
+ *   Sec. 4.4 coarse points at the cell means; for every point the closest
+ *            point on the candidate triangles (3-cliques of the coarse graph
+ *            with area above 1e-12 times the squared mean edge length) at its
+ *            own cell's sample, with barycentric weights (ties to the
+ *            lexicographically smallest triangle), inverse-distance weights
+ *            over the three closest of the sample and its coarse neighbours
+ *            when there is no candidate triangle, and the sample's own row
+ *            made the identity for a coarse column left empty.
+ * X: 3n host doubles (point i at X[3i..3i+2]); rowptr (n + 1), col: the
+ * symmetric neighbour graph (host CSR, sorted columns, no self loops).
+ * 0 < phi < 1 (the paper uses 1/8).  *out receives a host-side record of
+ * every level (release with gmg_destroy_hierarchy); device memory is used only
+ * during the call.  Errors: INVALID_ARG, NONFINITE, TOO_LARGE (a 2-ring of
+ * more than 96 points, a cell bordering more than 512 cells, a sample with
+ * more than 63 coarse neighbours), OOM, CUDA. */
+typedef struct gmg_hier_ctx *gmg_hierarchy;
+gmg_status gmg_build_hierarchy(gmg_hierarchy *out, int64_t n, const double *X, const int64_t *rowptr,
+                               const int32_t *col, double phi, int64_t stop, int max_levels, void *stream);
+/* Number of prolongations built and the construction's GPU time in ms
+ * (either output may be NULL). */
+gmg_status gmg_hierarchy_info(gmg_hierarchy h, int *n_prolong, double *build_ms);
+/* Level l's record (host outputs, each may be NULL): sizes; P_l as three
+ * (index, weight) slots per fine row (idx, w: 3 n_fine, the layout gmg_setup
+ * takes); the samples (fine index of every coarse point, n_coarse), the cell
+ * of every fine point (n_fine), the coarse points (3 n_coarse), the coarse
+ * neighbour graph (graph_rowptr n_coarse + 1, graph_col graph_nnz), and
+ * stats = {fallback rows, repaired columns, single-entry rows, samples}. */
+gmg_status gmg_hierarchy_level(gmg_hierarchy h, int l, int64_t *n_fine, int64_t *n_coarse, int64_t *graph_nnz,
+                               int32_t *idx, double *w, int32_t *samples, int32_t *cell, double *Xc,
+                               int64_t *graph_rowptr, int32_t *graph_col, int64_t *stats);
+/* Releases the record (NULL accepted). */
+gmg_status gmg_destroy_hierarchy(gmg_hierarchy h);
+
 /* ---- many independent systems (meshes of uneven size) in one batch ---- */
 typedef struct gmg_many_ctx *gmg_many;
 
-/* Sets up `nmesh` hierarchies: mesh k has system A[k] and the n_prolong[k]
- * prolongations P[k][0..] (host arrays, as for gmg_setup).  Errors: those of
- * gmg_setup for the failing mesh (the message names it). */
+/* Alg. 1 setup for `nmesh` systems: mesh k has system A[k] and the
+ * n_prolong[k] prolongations P[k][0..] (host arrays, as for gmg_setup, with
+ * the library's colourings).  Errors: those of gmg_setup for the failing mesh
+ * (the message names it). */
 gmg_status gmg_setup_many(gmg_many *m, int nmesh, const gmg_csr *A, const int *n_prolong,
                           const gmg_prolong *const *P, const gmg_options *opt, void *stream);
 
-/* Solves every mesh's n_k x nrhs system A_k X_k = B_k (row-major, host or
- * device per `mem`; B[k], X[k] per mesh, X holding the initial guesses) to
- * ||B - A X||_2 <= tol ||B||_2 per column, with FP32 V-cycles inside FP64
- * refinement.  Every outer iteration is one CUDA-graph launch in which all
- * meshes' cycles run concurrently.  info (NULL or nmesh entries) receives the
- * iteration count and the worst column's relative residual per mesh.
+/* Alg. 1 for many independent systems at once (the paper solves one system
+ * at a time; the batch is this library's addition): solves every mesh's
+ * n_k x nrhs system A_k X_k = B_k (row-major, host or device per `mem`; B[k],
+ * X[k] per mesh, X holding the initial guesses) to ||B - A X||_2 <= tol ||B||_2
+ * per column, with FP32 V-cycles (Alg. 2, multi-right-hand-side kernels)
+ * inside FP64 refinement.  The whole solve is one CUDA-graph launch: a
+ * conditional WHILE node repeats an iteration in which every mesh that has
+ * not converged runs its cycle (one conditional IF node per mesh, all
+ * concurrent) and a device-side check updates each mesh's residual and
+ * iteration count.  info (NULL or nmesh entries) receives the iteration count
+ * and the worst column's relative residual per mesh; each mesh stops at its
+ * own convergence.  Where the CUDA driver refuses conditional nodes, one
+ * graph per iteration runs every mesh until all have converged.
  * 1 <= nrhs <= 16. */
 gmg_status gmg_solve_many(gmg_many m, int nrhs, const double *const *B, double *const *X, double tol, int mem,
                           gmg_solve_info *info, void *stream);
+
+/* gmg_autotune_batched for every mesh of the batch (blocks of nrhs
+ * columns); the batch's captured iterations for that width are rebuilt on the
+ * next solve. */
+gmg_status gmg_autotune_many(gmg_many m, int nrhs, void *stream);
 
 /* Releases the batch (NULL accepted). */
 gmg_status gmg_destroy_many(gmg_many m);
@@ -249,6 +308,18 @@ gmg_status gmg_autotune(gmg_handle h, int *lanes_out, void *stream);
  * makes the launch sequence independent of timing.  Drops captured graphs
  * like gmg_autotune; synchronous. */
 gmg_status gmg_set_lanes(gmg_handle h, const int *lanes);
+
+/* Launch-shape autotuner of the multi-right-hand-side kernels (the batched
+ * and many-mesh solves) for blocks of nrhs columns (rounded up to 1, 2, 4, 8
+ * or 16): for every level with Gauss-Seidel sweeps, times four sweeps and a
+ * residual (captured in a CUDA graph) with each row split over G = 1, 2, 4 and
+ * 8 warps, and keeps the fastest G for that level and block width.  The
+ * split changes only the summation order of a row.  Synchronises `stream`;
+ * overwrites the batched work vectors.  lanes_out: NULL or nlev - 1 ints. */
+gmg_status gmg_autotune_batched(gmg_handle h, int nrhs, int *lanes_out, void *stream);
+/* Sets that split for blocks of nrhs columns (lanes: nlev - 1 ints, each 1,
+ * 2, 4 or 8; GMG_ERR_INVALID_ARG otherwise, nothing changed). */
+gmg_status gmg_set_lanes_batched(gmg_handle h, int nrhs, const int *lanes);
 
 /* ---- kernel timing (measurement support, not part of the method) ----
  * With profiling enabled, gmg_solve records CUDA events on its stream around

@@ -30,6 +30,8 @@ EXPORTED = [
     "gmg_profile_read", "gmg_kernel_launches", "gmg_residual_norm_noalloc", "gmg_setup_ML", "gmg_set_t",
     "gmg_mass", "gmg_grad", "gmg_setup_many", "gmg_solve_many", "gmg_destroy_many", "gmg_autotune", "gmg_set_lanes",
     "gmg_vcycle_batched", "gmg_pivot_reciprocal", "gmg_profile_levels", "gmg_grad_pattern",
+    "gmg_autotune_batched", "gmg_set_lanes_batched", "gmg_autotune_many",
+    "gmg_build_hierarchy", "gmg_hierarchy_info", "gmg_hierarchy_level", "gmg_destroy_hierarchy",
 ]
 
 
@@ -108,6 +110,13 @@ def load_library(path: str | None = None):
         "gmg_setup_many": (I, [V, I, V, V, V, V, V]),
         "gmg_autotune": (I, [V, V, V]),
         "gmg_set_lanes": (I, [V, V]),
+        "gmg_autotune_batched": (I, [V, I, V, V]),
+        "gmg_set_lanes_batched": (I, [V, I, V]),
+        "gmg_autotune_many": (I, [V, I, V]),
+        "gmg_build_hierarchy": (I, [V, I64, V, V, V, D, I64, I, V]),
+        "gmg_hierarchy_info": (I, [V, V, V]),
+        "gmg_hierarchy_level": (I, [V, I, V, V, V, V, V, V, V, V, V, V, V]),
+        "gmg_destroy_hierarchy": (I, [V]),
         "gmg_solve_many": (I, [V, I, V, V, D, I, V, V]),
         "gmg_destroy_many": (I, [V]),
         "gmg_profile_read": (I, [V, V]),
@@ -310,6 +319,16 @@ class Solver:
         arr = (ctypes.c_int * max(1, self.nlev - 1))(*[int(v) for v in lanes])
         _check(self._lib.gmg_set_lanes(self._h, arr), "gmg_set_lanes")
 
+    def autotune_batched(self, nrhs: int):
+        """Picks the multi-right-hand-side kernels' split per level for nrhs columns."""
+        lanes = (ctypes.c_int * max(1, self.nlev - 1))()
+        _check(self._lib.gmg_autotune_batched(self._h, int(nrhs), lanes, _stream()), "gmg_autotune_batched")
+        return list(lanes)[: self.nlev - 1]
+
+    def set_lanes_batched(self, nrhs: int, lanes):
+        arr = (ctypes.c_int * max(1, self.nlev - 1))(*[int(v) for v in lanes])
+        _check(self._lib.gmg_set_lanes_batched(self._h, int(nrhs), arr), "gmg_set_lanes_batched")
+
     def profile(self, enable: bool = True):
         _check(self._lib.gmg_profile(self._h, int(enable)), "gmg_profile")
 
@@ -426,6 +445,10 @@ class SolverMany:
             _check(st, "gmg_solve_many")
         return Xs, [i.iters for i in info], [i.rel_res for i in info], st
 
+    def autotune(self, nrhs: int):
+        """Autotunes every mesh's multi-right-hand-side kernels for nrhs columns."""
+        _check(self._lib.gmg_autotune_many(self._h, int(nrhs), _stream()), "gmg_autotune_many")
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             self._lib.gmg_destroy_many(self._h)
@@ -436,3 +459,47 @@ class SolverMany:
             self.close()
         except Exception:
             pass
+
+
+class BuiltLevel:
+    """One level of a hierarchy built on the GPU (gmg_build_hierarchy): the
+    prolongation in the layout Solver takes (n_coarse, idx [n, 3], w [n, 3])
+    and the construction's by-products."""
+
+    def __init__(self, n_fine, n_coarse, idx, w, samples, cell, Xc, graph_rowptr, graph_col, stats):
+        self.n_fine, self.n_coarse = n_fine, n_coarse
+        self.idx, self.w = idx, w
+        self.samples, self.cell, self.Xc = samples, cell, Xc
+        self.graph_rowptr, self.graph_col = graph_rowptr, graph_col
+        self.stats = dict(fallback=int(stats[0]), repaired=int(stats[1]), single=int(stats[2]), seeds=int(stats[3]))
+
+
+def build_hierarchy(X, rowptr, col, phi: float = 1.0 / 8.0, stop: int = 1000, max_levels: int = 24):
+    """The hierarchy construction of Sec. 4 on the GPU.  X: [n, 3] points;
+    (rowptr, col): the symmetric neighbour graph.  Returns (levels, GPU ms)."""
+    lib = load_library()
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(lib.gmg_build_hierarchy(ctypes.byref(h), X.shape[0], _np_ptr(X), _np_ptr(rp), _np_ptr(ci), float(phi),
+                                   int(stop), int(max_levels), _stream()), "gmg_build_hierarchy")
+    try:
+        nP, ms = ctypes.c_int(), ctypes.c_double()
+        _check(lib.gmg_hierarchy_info(h, ctypes.byref(nP), ctypes.byref(ms)), "gmg_hierarchy_info")
+        out = []
+        for l in range(nP.value):
+            nf, nc, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+            _check(lib.gmg_hierarchy_level(h, l, ctypes.byref(nf), ctypes.byref(nc), ctypes.byref(nnz), None, None,
+                                           None, None, None, None, None, None), "gmg_hierarchy_level")
+            nf, nc, nnz = nf.value, nc.value, nnz.value
+            idx, w = np.empty((nf, 3), np.int32), np.empty((nf, 3))
+            samples, cell, Xc = np.empty(nc, np.int32), np.empty(nf, np.int32), np.empty((nc, 3))
+            grp, gcol, st = np.empty(nc + 1, np.int64), np.empty(nnz, np.int32), np.empty(4, np.int64)
+            _check(lib.gmg_hierarchy_level(h, l, None, None, None, _np_ptr(idx), _np_ptr(w), _np_ptr(samples),
+                                           _np_ptr(cell), _np_ptr(Xc), _np_ptr(grp), _np_ptr(gcol), _np_ptr(st)),
+                   "gmg_hierarchy_level")
+            out.append(BuiltLevel(nf, nc, idx, w, samples, cell, Xc, grp, gcol, st))
+        return out, ms.value
+    finally:
+        lib.gmg_destroy_hierarchy(h)

@@ -277,6 +277,9 @@ gmg_status gmg_destroy(gmg_handle h) {
     if (e) cudaEventDestroy(e);
   if (h->h_scal) cudaFreeHost(h->h_scal);
   cudaDeviceSynchronize();
+  if (h->inv_stream) cudaStreamDestroy(h->inv_stream);
+  if (h->ev_gal) cudaEventDestroy(h->ev_gal);
+  if (h->ev_inv) cudaEventDestroy(h->ev_inv);
   h->arena.release();
   delete h;
   return GMG_OK;
@@ -321,9 +324,10 @@ gmg_status gmg_set_values(gmg_handle h, const double* val, int mem, void* stream
   }
   cudaStream_t s = (cudaStream_t)stream;
   Level& L0 = h->L[0];
+  GMG_TRY(join_inverse(h, s, false));  // a previous refresh's inverse still reads the level values
   GMG_CK(cudaMemcpyAsync(L0.csr_val, val, sizeof(double) * (size_t)L0.nnz,
                          mem == GMG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
-  return numeric_setup(h, s);
+  return numeric_setup(h, s, true);
 }
 
 gmg_status gmg_solve(gmg_handle h, const double* b, double* x, double tol, int mem, gmg_solve_info* info,
@@ -364,6 +368,10 @@ gmg_status gmg_solve(gmg_handle h, const double* b, double* x, double tol, int m
       set_error("gmg_solve: non-finite initial residual");
       st = GMG_ERR_NONFINITE;
     } else {
+      // a CG start joins a pending coarsest inverse right before its first
+      // coarse solve (its down-leg overlaps the inverse); the other modes
+      // join before their first iteration
+      if (!is_pcg(mode)) GMG_TRY(join_inverse(c, s, false));
       if (is_pcg(mode)) GMG_TRY(pcg_start(c, mode, s));
       bool fresh = true;  // CG: no step since the (re)start
       while (k < c->opt.max_iter) {
@@ -411,6 +419,7 @@ gmg_status gmg_solve(gmg_handle h, const double* b, double* x, double tol, int m
     info->iters = k;
     info->rel_res = rel;
   }
+  GMG_TRY(inverse_status(c, s));  // the pivot check of an inverse this solve joined
   return st;
 }
 
@@ -671,6 +680,7 @@ gmg_status gmg_coarse_solve(gmg_handle h, int fp32, const double* b, double* x, 
   GMG_TRY(check_handle(h));
   if (!b || !x) return GMG_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  GMG_TRY(join_inverse(h, s, true));
   const int l = h->nlev - 1;
   Level& C = h->L[l];
   GMG_TRY(to_level(h, l, fp32, b, C.b64, C.b32, s));
@@ -683,6 +693,7 @@ gmg_status gmg_vcycle(gmg_handle h, int fp32, const double* b, double* x, void* 
   GMG_TRY(check_handle(h));
   if (!b || !x) return GMG_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  GMG_TRY(join_inverse(h, s, true));
   Level& L = h->L[0];
   GMG_TRY(to_level(h, 0, fp32, b, L.b64, L.b32, s));
   GMG_TRY(to_level(h, 0, fp32, x, L.x64, L.x32, s));

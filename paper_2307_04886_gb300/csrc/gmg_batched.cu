@@ -49,65 +49,112 @@ __device__ __forceinline__ void store_row(float* __restrict__ p, const float (&o
   }
 }
 
-template <int NR>
+// One warp's share of a slice row for a launch that splits every row over G
+// warps (warp `part` takes entries k = part, part + G, ...); 8 / G slices per
+// block of 256 threads.
+struct MRow {
+  bool active;
+  int nk;
+  int64_t e, r;
+};
+template <int G>
+__device__ __forceinline__ MRow m_row(int64_t s, int64_t s_end, const int64_t* __restrict__ ptr,
+                                      const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow, int part,
+                                      int lane) {
+  MRow m{false, 0, 0, 0};
+  if (s < s_end) {
+    m.active = lane < nrow[s];
+    const int64_t e0 = ptr[s];
+    const int w = (int)((ptr[s + 1] - e0) >> 5);
+    m.nk = (m.active && part < w) ? (w - part + G - 1) / G : 0;
+    m.e = e0 + (int64_t)part * 32 + lane;
+    m.r = row0[s] + lane;
+  }
+  return m;
+}
+
+// acc[c] += sum over this warp's entries of a_rk X[k][c], entries in order.
+template <int NR, int G>
+__device__ __forceinline__ void m_dot(const MRow& m, const int32_t* __restrict__ col, const float* __restrict__ val,
+                                      const float* X, float (&acc)[NR]) {
+  int64_t e = m.e;
+  for (int q = 0; q < m.nk; ++q, e += (int64_t)G * 32) {
+    const float a = val[e];
+    float xv[NR];
+    load_row<NR>(X + (int64_t)col[e] * NR, xv);
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[c] += a * xv[c];
+  }
+}
+
+// Adds the other G - 1 warps' partial sums to row part 0's, in warp order.
+template <int NR, int G>
+__device__ __forceinline__ void m_combine(float (&acc)[NR], int warp, int lane) {
+  if constexpr (G > 1) {
+    __shared__ float red[8][NR][32];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) red[warp][c][lane] = acc[c];
+    __syncthreads();
+    if (warp % G == 0)
+      for (int g = 1; g < G; ++g)
+#pragma unroll
+        for (int c = 0; c < NR; ++c) acc[c] += red[warp + g][c][lane];
+  }
+}
+
+// One colour of a multi-right-hand-side Gauss-Seidel sweep, rows split over G warps.
+template <int NR, int G>
 __global__ void __launch_bounds__(256) k_gs_m(int64_t s0, int64_t s1, const int64_t* __restrict__ ptr,
                                               const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
                                               const int32_t* __restrict__ col, const float* __restrict__ val,
                                               const float* __restrict__ dinv, const float* __restrict__ B, float* X) {
-  const int64_t s = s0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (s >= s1 || lane >= nrow[s]) return;
-  const int64_t r = row0[s] + lane;
-  const int64_t e0 = ptr[s];
-  const int w = (int)((ptr[s + 1] - e0) >> 5);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, part = warp % G;
+  const int64_t s = s0 + (int64_t)blockIdx.x * (8 / G) + warp / G;
+  const MRow m = m_row<G>(s, s1, ptr, row0, nrow, part, lane);
   float acc[NR];
 #pragma unroll
   for (int c = 0; c < NR; ++c) acc[c] = 0.f;
-  int64_t e = e0 + lane;
-  for (int k = 0; k < w; ++k, e += 32) {
-    const float a = val[e];
-    float xv[NR];
-    load_row<NR>(X + (int64_t)col[e] * NR, xv);  // other colours: not written by this launch
+  m_dot<NR, G>(m, col, val, X, acc);  // other colours: not written by this launch
+  m_combine<NR, G>(acc, warp, lane);
+  if (part == 0 && m.active) {
+    float bv[NR];
+    load_row<NR>(B + m.r * NR, bv);
+    const float d = dinv[m.r];
 #pragma unroll
-    for (int c = 0; c < NR; ++c) acc[c] += a * xv[c];
+    for (int c = 0; c < NR; ++c) acc[c] = (bv[c] - acc[c]) * d;
+    store_row<NR>(X + m.r * NR, acc);
   }
-  float bv[NR];
-  load_row<NR>(B + r * NR, bv);
-  const float d = dinv[r];
-#pragma unroll
-  for (int c = 0; c < NR; ++c) acc[c] = (bv[c] - acc[c]) * d;
-  store_row<NR>(X + r * NR, acc);
 }
 
-template <int NR>
+// R = B - A X over all slices, rows split over G warps.
+template <int NR, int G>
 __global__ void __launch_bounds__(256) k_residual_m(int64_t nslice, const int64_t* __restrict__ ptr,
                                                     const int32_t* __restrict__ row0, const int32_t* __restrict__ nrow,
                                                     const int32_t* __restrict__ col, const float* __restrict__ val,
                                                     const float* __restrict__ diag, const float* __restrict__ X,
                                                     const float* __restrict__ B, float* __restrict__ R) {
-  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (s >= nslice || lane >= nrow[s]) return;
-  const int64_t r = row0[s] + lane;
-  const int64_t e0 = ptr[s];
-  const int w = (int)((ptr[s + 1] - e0) >> 5);
-  float acc[NR], xv[NR];
-  load_row<NR>(X + r * NR, xv);
-  const float d = diag[r];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, part = warp % G;
+  const int64_t s = (int64_t)blockIdx.x * (8 / G) + warp / G;
+  const MRow m = m_row<G>(s, nslice, ptr, row0, nrow, part, lane);
+  float acc[NR];
 #pragma unroll
-  for (int c = 0; c < NR; ++c) acc[c] = d * xv[c];
-  int64_t e = e0 + lane;
-  for (int k = 0; k < w; ++k, e += 32) {
-    const float a = val[e];
-    load_row<NR>(X + (int64_t)col[e] * NR, xv);
+  for (int c = 0; c < NR; ++c) acc[c] = 0.f;
+  if (part == 0 && m.active) {
+    float xv[NR];
+    load_row<NR>(X + m.r * NR, xv);
+    const float d = diag[m.r];
 #pragma unroll
-    for (int c = 0; c < NR; ++c) acc[c] += a * xv[c];
+    for (int c = 0; c < NR; ++c) acc[c] = d * xv[c];
   }
-  float bv[NR];
-  load_row<NR>(B + r * NR, bv);
+  m_dot<NR, G>(m, col, val, X, acc);
+  m_combine<NR, G>(acc, warp, lane);
+  if (part == 0 && m.active) {
+    float bv[NR];
+    load_row<NR>(B + m.r * NR, bv);
 #pragma unroll
-  for (int c = 0; c < NR; ++c) acc[c] = bv[c] - acc[c];
-  store_row<NR>(R + r * NR, acc);
+    for (int c = 0; c < NR; ++c) acc[c] = bv[c] - acc[c];
+    store_row<NR>(R + m.r * NR, acc);
+  }
 }
 
 template <int NR>
@@ -275,6 +322,49 @@ static inline int gblk(int64_t n) { return (int)std::max<int64_t>(1, std::min<in
 
 #define LCK() GMG_LAUNCHED()
 
+// The warps-per-row split of a level's multi-right-hand-side sweeps and
+// residual for NR columns: the autotuned or set choice, else a default by the
+// level's mean row length (about 8 entries per warp).
+template <int NR>
+static int m_lanes(const Level& L) {
+  const int v = L.mlanes[nr_index(NR)];
+  if (v > 0) return v;
+  const double mean = L.n > 0 ? (double)L.nnz / (double)L.n : 1.0;
+  return mean <= 12 ? 1 : mean <= 24 ? 2 : mean <= 48 ? 4 : 8;
+}
+
+template <int NR>
+static gmg_status sweep_m(Level& L, int k, cudaStream_t s, int G = 0) {
+  const int64_t s0 = L.color_slice_off[k], s1 = L.color_slice_off[k + 1];
+  if (s1 <= s0) return GMG_OK;
+  if (G == 0) G = m_lanes<NR>(L);
+  const int64_t grid = (s1 - s0 + 8 / G - 1) / (8 / G);
+  const Ell& A = L.A;
+  switch (G) {
+    case 1: k_gs_m<NR, 1><<<(unsigned)grid, 256, 0, s>>>(s0, s1, A.ptr, A.row0, A.nrow, A.col, A.v32, L.dinv32, L.B32, L.X32); break;
+    case 2: k_gs_m<NR, 2><<<(unsigned)grid, 256, 0, s>>>(s0, s1, A.ptr, A.row0, A.nrow, A.col, A.v32, L.dinv32, L.B32, L.X32); break;
+    case 4: k_gs_m<NR, 4><<<(unsigned)grid, 256, 0, s>>>(s0, s1, A.ptr, A.row0, A.nrow, A.col, A.v32, L.dinv32, L.B32, L.X32); break;
+    default: k_gs_m<NR, 8><<<(unsigned)grid, 256, 0, s>>>(s0, s1, A.ptr, A.row0, A.nrow, A.col, A.v32, L.dinv32, L.B32, L.X32);
+  }
+  LCK();
+  return GMG_OK;
+}
+
+template <int NR>
+static gmg_status residual_m(Level& L, cudaStream_t s, int G = 0) {
+  if (G == 0) G = m_lanes<NR>(L);
+  const Ell& A = L.A;
+  const int64_t grid = std::max<int64_t>(1, (A.nslice + 8 / G - 1) / (8 / G));
+  switch (G) {
+    case 1: k_residual_m<NR, 1><<<(unsigned)grid, 256, 0, s>>>(A.nslice, A.ptr, A.row0, A.nrow, A.col, A.v32, L.diag32, L.X32, L.B32, L.R32); break;
+    case 2: k_residual_m<NR, 2><<<(unsigned)grid, 256, 0, s>>>(A.nslice, A.ptr, A.row0, A.nrow, A.col, A.v32, L.diag32, L.X32, L.B32, L.R32); break;
+    case 4: k_residual_m<NR, 4><<<(unsigned)grid, 256, 0, s>>>(A.nslice, A.ptr, A.row0, A.nrow, A.col, A.v32, L.diag32, L.X32, L.B32, L.R32); break;
+    default: k_residual_m<NR, 8><<<(unsigned)grid, 256, 0, s>>>(A.nslice, A.ptr, A.row0, A.nrow, A.col, A.v32, L.diag32, L.X32, L.B32, L.R32);
+  }
+  LCK();
+  return GMG_OK;
+}
+
 // MGI(X_l, B_l, l) on [n_l x NR] blocks.  Every level starts from X_l = 0
 // (the recursive calls of Alg. 2, and the correction cycle of the outer
 // refinement on the finest level) unless keep_x, which keeps the caller's
@@ -289,19 +379,9 @@ static gmg_status vcycle_m(gmg_ctx* c, int l, cudaStream_t s, bool keep_x = fals
   }
   Level& C = c->L[l + 1];
   if (!keep_x) GMG_CK(cudaMemsetAsync(L.X32, 0, sizeof(float) * (size_t)(L.n * NR), s));
-  auto sweep = [&](int k) -> gmg_status {
-    const int64_t s0 = L.color_slice_off[k], s1 = L.color_slice_off[k + 1];
-    if (s1 > s0)
-      k_gs_m<NR><<<nblk((s1 - s0) * 32), 256, 0, s>>>(s0, s1, L.A.ptr, L.A.row0, L.A.nrow, L.A.col, L.A.v32,
-                                                     L.dinv32, L.B32, L.X32);
-    LCK();
-    return GMG_OK;
-  };
   for (int it = 0; it < c->opt.nu_pre; ++it)
-    for (int k = 0; k < L.ncolor; ++k) GMG_TRY(sweep(k));
-  k_residual_m<NR><<<nblk(L.A.nslice * 32), 256, 0, s>>>(L.A.nslice, L.A.ptr, L.A.row0, L.A.nrow, L.A.col, L.A.v32,
-                                                        L.diag32, L.X32, L.B32, L.R32);
-  LCK();
+    for (int k = 0; k < L.ncolor; ++k) GMG_TRY(sweep_m<NR>(L, k, s));
+  GMG_TRY(residual_m<NR>(L, s));
   k_restrict_m<NR><<<nblk(L.R.nslice * 32), 256, 0, s>>>(L.R.nslice, L.R.ptr, L.R.row0, L.R.nrow, L.R.col, L.R.v32,
                                                         L.R32, C.B32);
   LCK();
@@ -309,7 +389,7 @@ static gmg_status vcycle_m(gmg_ctx* c, int l, cudaStream_t s, bool keep_x = fals
   k_prolong_m<NR><<<gblk(L.n), 256, 0, s>>>(L.n, L.p_idx, L.p_w32, C.X32, L.X32);
   LCK();
   for (int it = 0; it < c->opt.nu_post; ++it)
-    for (int q = 0; q < L.ncolor; ++q) GMG_TRY(sweep(c->opt.post_forward ? q : L.ncolor - 1 - q));
+    for (int q = 0; q < L.ncolor; ++q) GMG_TRY(sweep_m<NR>(L, c->opt.post_forward ? q : L.ncolor - 1 - q, s));
   return GMG_OK;
 }
 
@@ -467,6 +547,7 @@ extern "C" gmg_status gmg_solve_batched(gmg_handle h, int nrhs, const double* B,
   GMG_CK(cudaSetDevice(h->device));
   GMG_TRY(ensure_batched(h));
   cudaStream_t s = (cudaStream_t)stream;
+  GMG_TRY(join_inverse(h, s, true));
   if (nrhs == 1) return solve_m<1>(h, nrhs, B, X, tol, mem, info, s);
   if (nrhs == 2) return solve_m<2>(h, nrhs, B, X, tol, mem, info, s);
   if (nrhs <= 4) return solve_m<4>(h, nrhs, B, X, tol, mem, info, s);
@@ -503,11 +584,114 @@ extern "C" gmg_status gmg_vcycle_batched(gmg_handle h, int nrhs, const double* B
   GMG_CK(cudaSetDevice(h->device));
   GMG_TRY(ensure_batched(h));
   cudaStream_t s = (cudaStream_t)stream;
+  GMG_TRY(join_inverse(h, s, true));
   if (nrhs == 1) return vcycle_step_m<1>(h, nrhs, B, X, s);
   if (nrhs == 2) return vcycle_step_m<2>(h, nrhs, B, X, s);
   if (nrhs <= 4) return vcycle_step_m<4>(h, nrhs, B, X, s);
   if (nrhs <= 8) return vcycle_step_m<8>(h, nrhs, B, X, s);
   return vcycle_step_m<16>(h, nrhs, B, X, s);
+}
+
+namespace gmg {
+// Times every smoothed level's multi-right-hand-side sweeps (all colours, four
+// sweeps) and residual for NR columns with each warps-per-row split G, as
+// captured CUDA graphs (the way a solve runs them), and keeps the fastest G.
+template <int NR>
+static gmg_status autotune_m(gmg_ctx* c, int* lanes_out, cudaStream_t stream) {
+  GMG_CK(cudaStreamSynchronize(stream));
+  if (!c->g_stream) GMG_CK(cudaStreamCreateWithFlags(&c->g_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = c->g_stream;
+  cudaEvent_t e0, e1;
+  GMG_CK(cudaEventCreate(&e0));
+  GMG_CK(cudaEventCreate(&e1));
+  const uint64_t launches_before = g_launches;
+  gmg_status st = GMG_OK;
+  for (int l = 0; l + 1 < c->nlev && st == GMG_OK; ++l) {
+    Level& L = c->L[l];
+    if (cudaMemsetAsync(L.X32, 0, sizeof(float) * (size_t)(L.n * NR), cs) != cudaSuccess ||
+        cudaMemsetAsync(L.B32, 0, sizeof(float) * (size_t)(L.n * NR), cs) != cudaSuccess) {
+      st = GMG_ERR_CUDA;
+      break;
+    }
+    float best_ms = 1e30f;
+    int best = m_lanes<NR>(L);
+    for (int G : {1, 2, 4, 8}) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        st = GMG_ERR_CUDA;
+        break;
+      }
+      for (int sweep = 0; sweep < 4 && st == GMG_OK; ++sweep)
+        for (int k = 0; k < L.ncolor && st == GMG_OK; ++k) st = sweep_m<NR>(L, k, cs, G);
+      if (st == GMG_OK) st = residual_m<NR>(L, cs, G);
+      const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+      if (st == GMG_OK && ec == cudaSuccess && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
+        float ms = 0.f;
+        cudaGraphLaunch(ge, cs);  // warm-up
+        cudaEventRecord(e0, cs);
+        for (int rep = 0; rep < 3; ++rep) cudaGraphLaunch(ge, cs);
+        cudaEventRecord(e1, cs);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = GMG_ERR_CUDA;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st == GMG_OK && ms < best_ms) {
+          best_ms = ms;
+          best = G;
+        }
+      } else if (st == GMG_OK) {
+        set_error("gmg_autotune_batched: graph capture of the sweeps failed");
+        st = GMG_ERR_CUDA;
+      }
+      if (ge) cudaGraphExecDestroy(ge);
+      if (g) cudaGraphDestroy(g);
+    }
+    if (st == GMG_OK) L.mlanes[nr_index(NR)] = best;
+    if (lanes_out) lanes_out[l] = L.mlanes[nr_index(NR)];
+  }
+  g_launches = launches_before;  // timing launches are not the caller's work
+  cudaStreamSynchronize(cs);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+static int block_width(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16; }
+
+static gmg_status autotune_batched(gmg_ctx* c, int nrhs, int* lanes_out, cudaStream_t s) {
+  GMG_CK(cudaSetDevice(c->device));
+  GMG_TRY(ensure_batched(c));
+  switch (block_width(nrhs)) {
+    case 1: return autotune_m<1>(c, lanes_out, s);
+    case 2: return autotune_m<2>(c, lanes_out, s);
+    case 4: return autotune_m<4>(c, lanes_out, s);
+    case 8: return autotune_m<8>(c, lanes_out, s);
+    default: return autotune_m<16>(c, lanes_out, s);
+  }
+}
+}  // namespace gmg
+
+extern "C" gmg_status gmg_autotune_batched(gmg_handle h, int nrhs, int* lanes_out, void* stream) {
+  if (!h || nrhs < 1 || nrhs > kMaxRhs) {
+    set_error("gmg_autotune_batched: bad handle or nrhs (1..16)");
+    return GMG_ERR_INVALID_ARG;
+  }
+  return autotune_batched(h, nrhs, lanes_out, (cudaStream_t)stream);
+}
+
+extern "C" gmg_status gmg_set_lanes_batched(gmg_handle h, int nrhs, const int* lanes) {
+  if (!h || nrhs < 1 || nrhs > kMaxRhs || !lanes) {
+    set_error("gmg_set_lanes_batched: bad handle, nrhs (1..16) or null lanes");
+    return GMG_ERR_INVALID_ARG;
+  }
+  for (int l = 0; l + 1 < h->nlev; ++l)
+    if (lanes[l] != 1 && lanes[l] != 2 && lanes[l] != 4 && lanes[l] != 8) {
+      set_error("gmg_set_lanes_batched: level " + std::to_string(l) + " split " + std::to_string(lanes[l]) +
+                " is not 1, 2, 4 or 8");
+      return GMG_ERR_INVALID_ARG;
+    }
+  const int slot = nr_index(block_width(nrhs));
+  for (int l = 0; l + 1 < h->nlev; ++l) h->L[l].mlanes[slot] = lanes[l];
+  return GMG_OK;
 }
 
 // ------------------------------------------------------------------ many meshes
@@ -941,4 +1125,27 @@ extern "C" gmg_status gmg_solve_many(gmg_many m, int nrhs, const double* const* 
   if (nrhs <= 4) return many_solve<4>(m, nrhs, B, X, tol, mem, info, s);
   if (nrhs <= 8) return many_solve<8>(m, nrhs, B, X, tol, mem, info, s);
   return many_solve<16>(m, nrhs, B, X, tol, mem, info, s);
+}
+
+extern "C" gmg_status gmg_autotune_many(gmg_many m, int nrhs, void* stream) {
+  if (!m || nrhs < 1 || nrhs > kMaxRhs) {
+    set_error("gmg_autotune_many: bad batch or nrhs (1..16)");
+    return GMG_ERR_INVALID_ARG;
+  }
+  for (size_t k = 0; k < m->h.size(); ++k) {
+    gmg_status st = autotune_batched(m->h[k], nrhs, nullptr, (cudaStream_t)stream);
+    if (st != GMG_OK) {
+      std::string keep = gmg_last_error();
+      set_error("mesh " + std::to_string(k) + ": " + keep);
+      return st;
+    }
+  }
+  // the captured iterations hold the old launch shapes
+  const int slot = nr_index(block_width(nrhs));
+  if (m->loop[slot]) cudaGraphExecDestroy(m->loop[slot]);
+  if (m->graph[slot]) cudaGraphExecDestroy(m->graph[slot]);
+  m->loop[slot] = nullptr;
+  m->graph[slot] = nullptr;
+  m->loop_refused[slot] = false;
+  return GMG_OK;
 }

@@ -401,8 +401,10 @@ __device__ void iter_check(const double* sc, int* it, double* hist, cudaGraphCon
 // With `check` the last block also runs the convergence test of the
 // device-side loop.  Grid: kRedBlocks x 256.
 template <class Z>
-__global__ void __launch_bounds__(256) k_pcg_axpy(int64_t n, double* sc, const double* p, const double* q, double* x,
-                                                  double* r, double* rold, float* b32, Z* z0,
+__global__ void __launch_bounds__(256) k_pcg_axpy(int64_t n, double* sc, const double* __restrict__ p,
+                                                  const double* __restrict__ q, double* __restrict__ x,
+                                                  double* __restrict__ r, double* __restrict__ rold,
+                                                  float* __restrict__ b32, Z* __restrict__ z0,
                                                   const Z* __restrict__ dinv, int64_t n0,
                                                   double* __restrict__ partial, int* counter, int check, int* it,
                                                   double* hist, cudaGraphConditionalHandle h) {
@@ -411,6 +413,7 @@ __global__ void __launch_bounds__(256) k_pcg_axpy(int64_t n, double* sc, const d
   pdl_trigger();
   const double alpha = sc[S_RZ] / sc[S_PQ];
   double rr = 0.0;
+#pragma unroll 4
   for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
     const double ri = r[i];
     rold[i] = ri;
@@ -441,12 +444,14 @@ __global__ void __launch_bounds__(256) k_pcg_axpy(int64_t n, double* sc, const d
 // last block, which sets beta = num / rz_old and rz = r.z for the next
 // iteration.  Grid: kRedBlocks x 256.
 template <class Z>
-__global__ void __launch_bounds__(256) k_pcg_zdots(int64_t n, const Z* z, const double* r, const double* rold,
-                                                   double* __restrict__ partial, int* counter, double* sc) {
+__global__ void __launch_bounds__(256) k_pcg_zdots(int64_t n, const Z* __restrict__ z, const double* __restrict__ r,
+                                                   const double* __restrict__ rold, double* __restrict__ partial,
+                                                   int* counter, double* sc) {
   __shared__ double red[256];
   pdl_wait();
   pdl_trigger();
   double num = 0.0, rz = 0.0;
+#pragma unroll 4
   for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
     const double zi = (double)z[i], ri = r[i];
     num += zi * (ri - rold[i]);
@@ -469,7 +474,7 @@ __global__ void __launch_bounds__(256) k_pcg_zdots(int64_t n, const Z* z, const 
 
 // p = z + beta p.
 template <class Z>
-__global__ void k_pcg_dir(int64_t n, const double* sc, const Z* z, double* p) {
+__global__ void k_pcg_dir(int64_t n, const double* sc, const Z* __restrict__ z, double* __restrict__ p) {
   pdl_wait();
   pdl_trigger();
   const double beta = sc[S_BETA];
@@ -840,6 +845,15 @@ gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s, bool c0_done, T* x_in, cons
   bool whole = l == c->nlev - 1;
   if constexpr (std::is_same<T, float>::value) whole = whole || (c->tail_l0 > 0 && l == c->tail_l0);
   if (whole) {  // the coarsest solve, or the cluster tail from this level down
+    if (c->inv_pending) {  // a refresh's coarsest inverse may still be running: wait for it here
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      GMG_CK(cudaStreamIsCapturing(s, &cs));
+      if (cs != cudaStreamCaptureStatusNone) {
+        set_error("internal: coarsest inverse pending during a graph capture");
+        return GMG_ERR_CUDA;
+      }
+      GMG_TRY(join_inverse(c, s, false));
+    }
     if (lp) {
       GMG_CK(record_timing_event(E[0], s));
       c->lev_kind[l] = 2;

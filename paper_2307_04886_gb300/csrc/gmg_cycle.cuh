@@ -5,7 +5,10 @@
 
 namespace gmg {
 
-gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s);
+// Galerkin values, solve layout and coarsest inverse for the current level-0
+// values.  With `defer` the inverse runs on the handle's own stream and the
+// call returns once the Galerkin values are checked; later calls join it.
+gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s, bool defer = false);
 gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P, const int32_t* const* coloring,
                       cudaStream_t s);
 

@@ -19,6 +19,8 @@ constexpr int kMaxRowEntries = 768; // Galerkin row limit (3/4 of the table)
 constexpr int64_t kMaxCoarse = 8192;
 constexpr int kRedBlocks = 608;     // fixed grid of the deterministic reductions (4 x 152 SMs)
 constexpr int kMaxRhs = 16;
+// Index of a multi-right-hand-side block width NR (1, 2, 4, 8, 16) in per-width tables.
+constexpr int nr_index(int NR) { return NR == 1 ? 0 : NR == 2 ? 1 : NR == 4 ? 2 : NR == 8 ? 3 : 4; }
 
 void set_error(const std::string& msg);
 
@@ -138,6 +140,8 @@ struct Level {
   int64_t n = 0, nnz = 0;
   int ncolor = 0;
   int lanes = 1;   // warps sharing one row in Gauss-Seidel (1, 2, 4, 8)
+  int mlanes[5] = {0, 0, 0, 0, 0};  // the same for the multi-right-hand-side kernels, by block width
+                                    // NR = 1, 2, 4, 8, 16 (0: default by mean row length)
   int rlanes = 1;  // the same for the residual (all rows at once, so more parallel)
   std::vector<int64_t> color_off;        // host: first permuted row of each colour (+ end)
   std::vector<int64_t> color_slice_off;  // host: first slice of each colour (+ end)
@@ -281,6 +285,13 @@ struct gmg_ctx {
   double* dhist = nullptr;        // relative residual per iteration (max_iter + 1)
   cudaStream_t g_stream = nullptr;
   bool values_ready = false;
+  // the coarsest inverse of a numeric refresh runs on its own stream while the
+  // caller's next work starts; ev_inv marks its end, and until a call joins it
+  // (inv_pending) nothing may read the inverse; its pivot check is read at the
+  // join (inv_check)
+  cudaStream_t inv_stream = nullptr;
+  cudaEvent_t ev_gal = nullptr, ev_inv = nullptr;
+  bool inv_pending = false, inv_check = false;
   // kernel timing: events bracket the finest level's smoothing blocks
   // (0-1 pre, 2-3 post) and the whole cycle (4-5)
   bool prof = false;
@@ -299,6 +310,11 @@ struct gmg_ctx {
 };
 
 namespace gmg {
+// Makes `s` wait for a coarsest inverse still running on its own stream; with
+// `check` also reads its pivot check (host synchronisation).
+gmg_status join_inverse(gmg_ctx* c, cudaStream_t s, bool check);
+// Reads the pivot check of a joined inverse once (GMG_ERR_CHOLESKY on failure).
+gmg_status inverse_status(gmg_ctx* c, cudaStream_t s);
 // Whether a tail cluster of ncta CTAs with `smem` bytes of shared memory each
 // can be scheduled on the device (sets the kernel's attributes).
 gmg_status tail_configure(gmg_ctx* c, int ncta, int threads, int smem, bool* ok);

@@ -137,10 +137,11 @@ gmg_status gmg_set_t(gmg_handle h, double t, void* stream) {
   GMG_CK(cudaSetDevice(h->device));
   cudaStream_t s = (cudaStream_t)stream;
   Level& L0 = h->L[0];
+  GMG_TRY(join_inverse(h, s, false));  // a previous refresh's inverse still reads the level values
   k_ml_values<<<grid_of(L0.n), 256, 0, s>>>(L0.n, L0.csr_rowptr, h->ml_dpos, t, h->ml_L, h->ml_M, L0.csr_val);
   GMG_LAUNCHED();
   h->ml_t = t;
-  return numeric_setup(h, s);
+  return numeric_setup(h, s, true);
 }
 
 gmg_status gmg_mass(gmg_handle h, const double* u, double* out, void* stream) {

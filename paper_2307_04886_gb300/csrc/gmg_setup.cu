@@ -1257,7 +1257,31 @@ static gmg_status galerkin_symbolic(gmg_ctx* c, int l, cudaStream_t s, std::vect
 
 // Numeric part of every Galerkin level, value scatter into the solve layout,
 // and the coarsest factorisation.  Runs entirely on the GPU.
-gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s) {
+gmg_status join_inverse(gmg_ctx* c, cudaStream_t s, bool check) {
+  if (c->inv_pending) {
+    GMG_CK(cudaStreamWaitEvent(s, c->ev_inv, 0));
+    c->inv_pending = false;
+    c->inv_check = true;
+  }
+  return check ? inverse_status(c, s) : GMG_OK;
+}
+
+gmg_status inverse_status(gmg_ctx* c, cudaStream_t s) {
+  if (!c->inv_check) return GMG_OK;
+  int h = 0;
+  GMG_CK(cudaMemcpyAsync(&h, c->dstatus + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GMG_CK(cudaStreamSynchronize(s));
+  c->inv_check = false;
+  if (h) {
+    set_error("coarsest operator not positive definite (sweep pivot <= 0)");
+    return GMG_ERR_CHOLESKY;
+  }
+  return GMG_OK;
+}
+
+gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s, bool defer) {
+  GMG_TRY(join_inverse(c, s, false));  // the previous inverse still reads the dense work matrix
+  c->inv_check = false;
   GMG_CK(cudaMemsetAsync(c->dstatus, 0, 2 * sizeof(int), s));
   for (int l = 0; l < c->nlev; ++l) {
     Level& F = c->L[l];
@@ -1283,7 +1307,16 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s) {
       GMG_LAUNCHED();
     }
   }
-  // coarsest: explicit inverse by block sweeps
+  // coarsest: explicit inverse by block sweeps (on the handle's own stream when deferred)
+  const cudaStream_t s_main = s;
+  if (defer) {
+    if (!c->inv_stream) GMG_CK(cudaStreamCreateWithFlags(&c->inv_stream, cudaStreamNonBlocking));
+    if (!c->ev_gal) GMG_CK(cudaEventCreateWithFlags(&c->ev_gal, cudaEventDisableTiming));
+    if (!c->ev_inv) GMG_CK(cudaEventCreateWithFlags(&c->ev_inv, cudaEventDisableTiming));
+    GMG_CK(cudaEventRecord(c->ev_gal, s));
+    GMG_CK(cudaStreamWaitEvent(c->inv_stream, c->ev_gal, 0));
+    s = c->inv_stream;
+  }
   Level& C = c->L[c->nlev - 1];
   const int n = (int)c->nco;
   const int nbk = (n + 31) / 32, npad = nbk * 32;
@@ -1306,7 +1339,15 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s) {
   GMG_TRY(launch(k_gj_finish, grid_for((int64_t)n * n, 256), 256, s, n, npad, (const double*)c->dense, c->Ainv,
                  c->Ainv32));
   int h[2] = {0, 0};
-  GMG_CK(cudaMemcpyAsync(h, c->dstatus, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (defer) {
+    // the Galerkin values are checked now; the inverse's pivot check at the join
+    GMG_CK(cudaEventRecord(c->ev_inv, s));
+    c->inv_pending = true;
+    s = s_main;
+    GMG_CK(cudaMemcpyAsync(h, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+  } else {
+    GMG_CK(cudaMemcpyAsync(h, c->dstatus, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
   GMG_CK(cudaStreamSynchronize(s));
   if (h[0] & 2) {
     set_error("non-finite value in a level operator");
@@ -1640,7 +1681,7 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   GMG_TRY(a.alloc(&c->dhist, (size_t)c->opt.max_iter + 2));
   GMG_CK(cudaMallocHost((void**)&c->h_scal, 64 * sizeof(double)));
   GMG_TRY(build_tail(c));
-  return numeric_setup(c, s);
+  return numeric_setup(c, s, false);
 }
 
 }  // namespace gmg
