@@ -9,4 +9,4 @@ each implement on their own.
 """
 from .hierarchy import Prolongation, build_hierarchy, build_level, compile_builder  # noqa: F401
 from .workloads import (System, cached, cached_batch, cloud_system, heat_system, icosphere_system,  # noqa: F401
-                        spheres_batch, torus_system, workload)
+                        is_cached, nonmanifold_system, spheres_batch, torus_system, workload)

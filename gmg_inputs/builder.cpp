@@ -103,12 +103,22 @@ Level* build_level(int64_t n, const double* Xp, const int64_t* rp, const int32_t
   auto X = [&](int64_t i) { return V3{Xp[3 * i], Xp[3 * i + 1], Xp[3 * i + 2]}; };
   Level* L = new Level();
 
-  // mean edge length over undirected edges
+  // mean edge length over undirected edges (i < j).  Summation order: the
+  // lengths of a row in pattern order, the rows of each block of 1024
+  // consecutive rows in order, then the block sums in order (a fixed order that
+  // a parallel builder reproduces exactly)
   double esum = 0;
   int64_t ecount = 0;
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
-      if (ci[k] > i) { esum += norm(sub(X(i), X(ci[k]))); ++ecount; }
+  for (int64_t b0 = 0; b0 < n; b0 += 1024) {
+    double bsum = 0;
+    for (int64_t i = b0; i < std::min<int64_t>(n, b0 + 1024); ++i) {
+      double rsum = 0;
+      for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+        if (ci[k] > i) { rsum += norm(sub(X(i), X(ci[k]))); ++ecount; }
+      bsum += rsum;
+    }
+    esum += bsum;
+  }
   const double ehat = ecount ? esum / ecount : 1.0;
   const double r = std::pow(phi, -1.0 / 3.0) * ehat;  // Eq. (sampling radius)
 

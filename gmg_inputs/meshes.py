@@ -3,7 +3,9 @@
 The paper evaluates on scanned meshes and point clouds (Sec. 5.3) that are not
 available here; these generators stand in for them at comparable sizes and
 structure (closed manifold triangle meshes with about 7 nonzeros per Laplacian
-row, and noisy point clouds with k-nearest-neighbour graphs).
+row, noisy point clouds with k-nearest-neighbour graphs, and a non-manifold
+triangle mesh whose spine edges border more than two triangles, the kind of
+input Sec. 5.4 smooths on non-manifold meshes).
 
 Nothing in this module performs any step of the multigrid method itself.
 """
@@ -151,3 +153,45 @@ def noisy_sphere_cloud(n: int, rng: np.random.Generator, sigma: float = 1e-3):
     u = g / np.linalg.norm(g, axis=1, keepdims=True)
     z = rng.standard_normal(n)
     return u * (1.0 + sigma * z)[:, None]
+
+
+def book(pages: int, n_radial: int, n_spine: int, height: float = 1.0, seed: int = 0, amount: float = 0.2):
+    """A non-manifold "book": `pages` rectangular sheets that share one spine
+    line (the z axis).  Sheet p lies in the half-plane at angle 2 pi p / pages
+    around the spine and is bent into a quarter-cylinder arc away from it;
+    vertex (i, j) of a sheet sits at radial index i = 0..n_radial-1 and spine
+    index j = 0..n_spine-1, and the i = 0 column is the shared spine (one vertex
+    per j for all sheets).  Every grid quad is split along the same diagonal,
+    so each spine edge borders one triangle of every sheet: `pages` triangles.  All vertices but the
+    spine are then jittered by U(-amount, amount) x mean edge length per
+    coordinate.  Returns (V, F, rng), rng advanced past the jitter draws."""
+    rng = np.random.default_rng(seed)
+    h = height / (n_spine - 1)
+    spine = np.stack([np.zeros(n_spine), np.zeros(n_spine), h * np.arange(n_spine)], axis=1)
+    V = [spine]
+    F = []
+    idx = lambda p, i, j: j if i == 0 else n_spine + p * (n_radial - 1) * n_spine + (i - 1) * n_spine + j
+    for p in range(pages):
+        th = 2.0 * np.pi * p / pages
+        d = np.array([np.cos(th), np.sin(th), 0.0])        # radial direction of the sheet
+        q = np.array([-np.sin(th), np.cos(th), 0.0])       # bending direction
+        i = np.arange(1, n_radial)[:, None]
+        j = np.arange(n_spine)[None, :]
+        s = i * h                                          # arc length from the spine
+        R = (n_radial - 1) * h * 2.0 / np.pi                # quarter circle over the sheet's width
+        a = s / R
+        pos = (R * np.sin(a))[..., None] * d + (R * (1.0 - np.cos(a)))[..., None] * q
+        pos = np.broadcast_to(pos, (n_radial - 1, n_spine, 3)).copy()
+        pos[..., 2] = (h * j) * np.ones_like(s)
+        V.append(pos.reshape(-1, 3))
+        for ii in range(n_radial - 1):
+            for jj in range(n_spine - 1):
+                a0, b0 = idx(p, ii, jj), idx(p, ii + 1, jj)
+                c0, d0 = idx(p, ii + 1, jj + 1), idx(p, ii, jj + 1)
+                F += [(a0, b0, c0), (a0, c0, d0)]
+    V = np.concatenate(V, axis=0)
+    F = np.asarray(F, dtype=np.int64)
+    e = mean_edge_length(V, mesh_edges(F))
+    J = rng.uniform(-amount, amount, size=V.shape) * e
+    J[:n_spine] = 0.0  # the spine stays straight (it is shared by every sheet)
+    return V + J, F, rng

@@ -13,6 +13,9 @@ prolongation hierarchy of Sec. 4 built on the surface's points and edges.
   heat512k    : jittered torus 1024 x 512 (524,288 vertices), t = 1e-3, u0 one-hot
                 at 16 random vertices, x_target ~ N(0, 1), seed 4
 
+  book5       : data smoothing on a non-manifold mesh (5 bent sheets sharing a spine,
+                149,200 vertices), t = 1e-3, seed 7
+
 Two further systems of the paper on jittered tori, with the same hierarchy recipe:
   poisson     : Eq. (Poisson) of Sec. 5.2, (S + eta M) x = M y with eta = 1e-6
                 (nearly singular: the constant mode has eigenvalue ~eta M)
@@ -103,6 +106,18 @@ def bilaplacian_system(n_major: int = 256, n_minor: int = 120, alpha: float = 1e
                   extra=dict(beta=np.array(beta)))
 
 
+def nonmanifold_system(pages: int = 5, n_radial: int = 150, n_spine: int = 200, t: float = 1e-3, seed: int = 7,
+                       stop: int = 1000):
+    """Data smoothing (M + t L) x = M y on the non-manifold book mesh
+    (meshes.book: `pages` bent sheets sharing one spine whose edges border
+    `pages` triangles), cotan Laplacian and lumped mass summed over every
+    triangle (both stay well defined on non-manifold edges), y ~ N(0, 1).  The
+    hierarchy of Sec. 4 is built on the mesh's edge graph."""
+    V, F, rng = meshes.book(pages, n_radial, n_spine, seed=seed)
+    y = rng.standard_normal(V.shape[0])
+    return _mesh_system(f"book{pages}x{n_radial}x{n_spine}", V, F, t, y, stop=stop)
+
+
 def cloud_system(n: int, k: int = 30, t: float = 1e-3, seed: int = 2, stop: int = 1000, graph_k: int = 6):
     """Point cloud: the system uses the k-nearest-neighbour Gaussian
     Laplacian; the hierarchy is built on the sparser union graph of the
@@ -178,6 +193,11 @@ def _load(path, name) -> System:
     return System(name, A, z["b"], Ps, z["Mdiag"] if "Mdiag" in z else None, L, float(z["t"]), extra)
 
 
+def is_cached(name: str) -> bool:
+    """Whether the named workload's inputs are in the cache already."""
+    return os.path.exists(os.path.join(_CACHE, name + ".npz")) or os.path.exists(os.path.join(_CACHE, name, "count"))
+
+
 def cached(name: str, maker, *args, **kw) -> System:
     os.makedirs(_CACHE, exist_ok=True)
     path = os.path.join(_CACHE, name + ".npz")
@@ -223,4 +243,6 @@ def workload(name: str) -> System:
         return cached(name, heat_system)
     if name == "cloud4m":
         return cached(name, cloud_system, 4194304)
+    if name == "book5":
+        return cached(name, nonmanifold_system)
     raise KeyError(name)

@@ -518,3 +518,63 @@ def test_caller_colouring_matches_oracle_with_it(gmg):
     with pytest.raises(gmg.GMGError) as e:
         gmg.Solver(s.A, s.Ps, coloring=bad)
     assert e.value.status == gmg.GMG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("split", [1, 2, 4, 8])
+def test_batched_split_rows_match_oracle(gmg, split):
+    """The multi-right-hand-side sweeps and residual with every row split over
+    1, 2, 4 or 8 warps (the shapes the batched autotuner chooses from) give the
+    oracle's cycle per column; the autotuner returns valid splits and a solve
+    after it reaches 1e-10."""
+    s = gi.torus_system(250, 122, 1e-4, 11)
+    o = oracle.Oracle(s.A, s.Ps)
+    g = gmg.Solver(s.A, s.Ps)
+    rng = np.random.default_rng(SEED + 70 + split)
+    X0 = rng.standard_normal((s.n, 5))
+    B = rng.standard_normal((s.n, 5)) * s.Mdiag[:, None]
+    g.set_lanes_batched(5, [split] * (g.nlev - 1))
+    X1 = _np(g.vcycle_batched(_t(X0), _t(B)))
+    for c in range(5):
+        close(X1[:, c], o.vcycle(X0[:, c], B[:, c]), 1e-6, f"split {split} column {c}", stencil_factor(s.A))
+    with pytest.raises(gmg.GMGError):
+        g.set_lanes_batched(5, [3] * (g.nlev - 1))
+    lanes = g.autotune_batched(5)
+    assert all(v in (1, 2, 4, 8) for v in lanes)
+    X, it, rr, _, st = g.solve_batched(_t(B), tol=1e-10)
+    Xn = _np(X)
+    assert st == 0 and max(np.linalg.norm(B - s.A @ Xn, axis=0) / np.linalg.norm(B, axis=0)) <= 1e-10
+    g.close()
+
+
+def test_refresh_defers_the_coarsest_inverse(gmg):
+    """A numeric refresh (gmg_set_values) returns once the Galerkin values are
+    checked and leaves the coarsest inverse running on its own stream; the next
+    solve waits for it right before its first coarse solve.  Refreshed solves
+    match the oracle built for the new values, and a refresh whose coarsest
+    operator is not positive definite is reported by the solve that follows."""
+    import scipy.sparse as sp
+
+    s = gi.icosphere_system(4)
+    g = gmg.Solver(s.A, s.Ps, precision=gmg.GMG_FP32_PCG)
+    for t in (3e-3, 1e-2):
+        At = (sp.diags(s.Mdiag) + t * s.L).tocsr()
+        At.sort_indices()
+        g.set_values(At.data)
+        x, it, rr, _, st = g.solve(_t(s.b), tol=1e-10)
+        assert st == 0 and np.linalg.norm(s.b - At @ _np(x)) <= 1e-10 * np.linalg.norm(s.b)
+        xo, _, _, ok = oracle.Oracle(At, s.Ps).solve(s.b, tol=1e-12, pcg=True)
+        close(_np(x), xo, 1e-8, f"solution after refresh t={t}")
+    g.close()
+    n = 40
+    good = _dense_spd(n, 7)
+    g = gmg.Solver(good, [], precision=gmg.GMG_FP64)
+    bad = good.copy().tolil()
+    bad[3, 4] = bad[4, 3] = 10.0 * good[3, 3]  # symmetric, positive diagonal, not positive definite
+    bad = bad.tocsr()
+    bad.sort_indices()
+    assert np.array_equal(bad.indices, good.indices)
+    g.set_values(bad.data)
+    with pytest.raises(gmg.GMGError) as e:
+        g.solve(_t(np.ones(n)), tol=1e-10)
+    assert e.value.status == gmg.GMG_ERR_CHOLESKY
+    g.close()

@@ -1,6 +1,7 @@
-"""CPU pins of the two further systems of the paper (Sec. 5.2 Eq. (Poisson),
-Sec. 5.5 bi-Laplacian smoothing) and of the oracle on them: the matrices
-against their definitions, closed forms, and a direct sparse solve."""
+"""CPU pins of the further systems of the paper (Sec. 5.2 Eq. (Poisson),
+Sec. 5.5 bi-Laplacian smoothing, Sec. 5.4 smoothing on a non-manifold mesh)
+and of the oracle on them: the matrices against their definitions, closed
+forms, and a direct sparse solve."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as sla
@@ -61,3 +62,54 @@ def test_oracle_matches_direct_solve(which, poisson, bilap):
     x, it, _, ok = o.solve(s.b, tol=tol, max_iter=100, pcg=True)
     assert ok
     assert np.linalg.norm(x - xe) <= 1e-6 * np.linalg.norm(xe)
+
+
+@pytest.fixture(scope="module")
+def book():
+    return gi.nonmanifold_system(3, 30, 40, stop=200)
+
+
+def test_book_mesh_is_non_manifold(book):
+    """Every spine edge of the book mesh borders one triangle of each of the 3
+    sheets (a manifold edge borders at most two), and the other edges at most
+    two."""
+    from gmg_inputs import meshes
+
+    V, F, _ = meshes.book(3, 30, 40, seed=7)
+    e = np.sort(np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]]), axis=1)
+    keys, counts = np.unique(e, axis=0, return_counts=True)
+    spine = (keys[:, 0] < 40) & (keys[:, 1] < 40)
+    assert spine.sum() == 39 and np.all(counts[spine] == 3)
+    assert np.all(counts[~spine] <= 2)
+
+
+def test_book_operators(book):
+    """On the non-manifold mesh the cotan Laplacian (a sum of per-triangle FEM
+    stiffness matrices) stays symmetric, annihilates constants and is
+    positive semi-definite; the lumped mass sums to the mesh area; so
+    A = M + t L is SPD and (M + t L) x = M 1 has the solution x = 1."""
+    s = book
+    L = s.L.toarray()
+    assert np.abs(L - L.T).max() == 0.0
+    assert np.abs(L @ np.ones(s.n)).max() <= 1e-12 * np.abs(L).max()
+    ev = np.linalg.eigvalsh(L)
+    assert ev[0] >= -1e-10 * ev[-1]
+    from gmg_inputs import meshes
+
+    V, F, _ = meshes.book(3, 30, 40, seed=7)
+    area = 0.5 * np.linalg.norm(np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]]), axis=1).sum()
+    assert abs(s.Mdiag.sum() - area) <= 1e-12 * area
+    o = oracle.Oracle(s.A, s.Ps)
+    x, it, _, ok = o.solve(s.Mdiag * np.ones(s.n), tol=1e-12)
+    assert ok and np.abs(x - 1.0).max() <= 1e-9
+
+
+def test_book_oracle_matches_direct_solve(book):
+    s = book
+    o = oracle.Oracle(s.A, s.Ps)
+    assert o.nlev >= 3
+    for pcg in (False, True):
+        x, it, hist, ok = o.solve(s.b, tol=1e-10, pcg=pcg)
+        assert ok
+        xe = sla.spsolve(s.A.tocsc(), s.b)
+        assert np.linalg.norm(x - xe) <= 1e-8 * np.linalg.norm(xe)
