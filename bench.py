@@ -20,9 +20,10 @@ full setup + solve per step, on all host cores).
 Beside the headline the JSON line carries, under config.workloads, the other
 synthetic workloads measured on the same GPU (--configs none skips them):
 icosphere5 (plain FP64 V-cycle iteration), heat512k (forward + adjoint solve of
-the differentiable heat diffusion), spheres64 (64 meshes x 8 right-hand sides
-in one many-mesh solve against 512 plain FP64 single solves) and cloud4m (the
-4M-point kNN cloud, with Gauss-Seidel GB/s per level).
+the differentiable heat diffusion), book5 (smoothing on a non-manifold mesh),
+spheres64 (64 meshes x 8 right-hand sides in one many-mesh solve against 512
+plain FP64 single solves) and cloud4m (the 4M-point kNN cloud, with
+Gauss-Seidel GB/s per level).
 """
 from __future__ import annotations
 
@@ -368,6 +369,7 @@ def other_workloads(g, names, steps):
             elif name == "spheres64":
                 systems = gi.cached_batch("spheres64", gi.spheres_batch)
                 many = g.SolverMany([(q.A, q.Ps) for q in systems])
+                many.autotune(int(systems[0].b.shape[1]))  # multi-right-hand-side row splits per mesh and level
                 Bs = [torch.tensor(q.b, device=dev) for q in systems]
                 Xs = [torch.zeros_like(B) for B in Bs]
                 out = {}
@@ -400,7 +402,27 @@ def other_workloads(g, names, steps):
                              "many_iterations_max": int(max(its)), "many_iterations_min": int(min(its)),
                              "plain_fp64_single_solves_ms": single_ms,
                              "speedup_vs_plain_fp64": single_ms / many_ms,
-                             "plain": "every column solved alone by the plain FP64 V-cycle iteration (gmg_solve)"}
+                             "plain": "every column solved alone by the plain FP64 V-cycle iteration (gmg_solve)",
+                             "shapes": "multi-right-hand-side row splits autotuned per mesh and level"}
+            elif name == "book5":
+                s = gi.workload(name)
+                b = torch.tensor(s.b, device=dev)
+                x = torch.zeros_like(b)
+                r = {"rows": s.n, "mesh": "non-manifold: 5 bent sheets sharing a spine (Sec. 5.4 stand-in)"}
+                for tag, prec in (("fp64_plain", g.GMG_FP64), ("fp32_pcg", g.GMG_FP32_PCG)):
+                    sv = g.Solver(s.A, s.Ps, precision=prec)
+                    sv.autotune()
+                    out = {}
+
+                    def run():
+                        x.zero_()
+                        out["r"] = sv.solve(b, x, tol=1e-10)
+
+                    _ev_ms(run, 3)
+                    r[f"{tag}_ms"] = _ev_ms(run, steps)
+                    r[f"{tag}_iterations"] = out["r"][1]
+                    sv.close()
+                res[name] = r
             elif name == "cloud4m":
                 s = gi.workload(name)
                 sv = g.Solver(s.A, s.Ps, precision=g.GMG_FP32_PCG)
@@ -444,8 +466,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gmg", choices=["gmg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--configs", default="icosphere5,heat512k,spheres64,cloud4m",
-                    help="comma-separated other workloads to time after the headline, or 'none'")
+    ap.add_argument("--configs", default="icosphere5,heat512k,book5,spheres64,cloud4m?",
+                    help="comma-separated other workloads to time after the headline, or 'none'; a trailing '?' "
+                         "times that workload only when its inputs are already cached (cloud4m takes minutes to "
+                         "generate on the host)")
     ap.add_argument("--profile-step", action="store_true",
                     help="set up, autotune, run `warmup` untimed steps and one step, print a short note and exit "
                          "(the launch sequence a kernel profiler lists; no timing is reported)")
@@ -455,10 +479,18 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
 
+    ws, rank, local = dist_env()
+    # inputs of the other workloads that take long to generate, prepared by a
+    # separate process while the headline runs
+    names = [] if args.configs == "none" else [c for c in args.configs.split(",") if c]
+    prep = None
+    if rank == 0 and "spheres64" in names:
+        prep = subprocess.Popen([sys.executable, "-c", "import gmg_inputs as gi; gi.cached_batch('spheres64', gi.spheres_batch)"],
+                                cwd=ROOT, stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+
     import numpy as np
     import torch
 
-    ws, rank, local = dist_env()
     if ws > 1:
         import torch.distributed as dist
 
@@ -598,10 +630,46 @@ def main():
         r["kernel"] = r["kernel"].replace("float", "double")
     traffic = ncu_traffic(kname, WORKLOAD)
 
+    # Sec. 4 hierarchy construction of the same mesh on the GPU, against the host builder
+    build_info = None
+    if rank == 0:
+        try:
+            from gmg_inputs import meshes, operators
+            from gmg_inputs.hierarchy import build_hierarchy as host_build
+
+            V, F, _ = meshes.jittered_torus(2048, 512, 1)
+            rp, ci = operators.edges_to_adjacency(V.shape[0], meshes.mesh_edges(F))
+            g.build_hierarchy(V, rp, ci)  # warm-up (module load, first allocations)
+            w0 = time.perf_counter()
+            lv, gpu_ms = g.build_hierarchy(V, rp, ci)
+            wall_ms = (time.perf_counter() - w0) * 1e3
+            w0 = time.perf_counter()
+            hPs = host_build(V, rp, ci)
+            host_ms = (time.perf_counter() - w0) * 1e3
+            same = len(hPs) == len(lv) and all(
+                np.array_equal(a.idx, b.idx) and np.array_equal(a.w, b.w) for a, b in zip(hPs, lv))
+            build_info = {"gpu_ms": gpu_ms, "gpu_call_wall_ms": wall_ms, "host_builder_ms": host_ms,
+                          "speedup": host_ms / wall_ms, "levels": [1048576] + [q.n_coarse for q in lv],
+                          "prolongations_identical_to_host_builder": bool(same),
+                          "what": "gmg_build_hierarchy (Sec. 4 sampling, Voronoi cells, coarse graph, triangles, "
+                                  "barycentric prolongation) on the torus1m mesh, phi = 1/8, stop at 1000"}
+        except Exception as e:
+            build_info = {"error": f"{type(e).__name__}: {e}"}
+
     extra = {}
-    names = [] if args.configs == "none" else [c for c in args.configs.split(",") if c]
+    if prep is not None:
+        prep.wait()
     if names and rank == 0:
-        extra = other_workloads(g, names, max(3, args.steps // 3))
+        chosen = []
+        for nm in names:
+            if nm.endswith("?"):
+                nm = nm[:-1]
+                if not gi.is_cached(nm):
+                    extra[nm] = {"skipped": "inputs not cached on this machine (generating them takes minutes); "
+                                            f"python bench.py --configs {nm} generates and times them"}
+                    continue
+            chosen.append(nm)
+        extra.update(other_workloads(g, chosen, max(3, args.steps // 3)))
 
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -630,6 +698,7 @@ def main():
             "wall_ms_timed_region": wall,
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
             "workloads": extra,
+            "hierarchy_build": build_info,
         },
         "roofline": {"bound": "hbm", "kernel": f"{kname} (levels {k_levels}, one colour per launch)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
