@@ -437,8 +437,9 @@ __device__ __forceinline__ void emit_entry(int64_t e, int64_t m, double x, doubl
 // plan's order (zero padding adds +0), then written with its mirror (exact
 // symmetry) into the CSR and the solve layout.  Terms are loaded B at a time
 // before they are added, so a long term list is not a chain of dependent
-// loads: B = 16 for the slices of long entries (hundreds of terms on coarse
-// levels; 128 registers, where B = 32 took 226 and halved the warps in
+// loads, and the plan of batch k + 1 is loaded while the gathered values of
+// batch k arrive: B = 16 for the slices of long entries (hundreds of terms
+// on coarse levels; B = 32 took 226 registers and halved the warps in
 // flight), B = 8 elsewhere (fewer registers, more warps in flight).  The
 // plan is read once, with the evict-first (streaming) hint, so that it does
 // not push the finer level's gathered values out of L2.
@@ -458,21 +459,37 @@ __global__ void __launch_bounds__(kGalThreads)
     const int64_t g = i >> 5, lane = i & 31;
     const int64_t base = sptr[g] + lane, width = (sptr[g + 1] - sptr[g]) >> 5;
     double acc = 0.0;
-    for (int64_t k0 = 0; k0 < width; k0 += B) {
-      int ed[B];
-      double cf[B], av[B];
+    int ed[B];
+    double cf[B];
 #pragma unroll
-      for (int j = 0; j < B; ++j)
-        if (k0 + j < width) {
-          ed[j] = __ldcs(sedge + base + (k0 + j) * 32);
-          cf[j] = __ldcs(scoef + base + (k0 + j) * 32);
-        }
+    for (int j = 0; j < B; ++j)
+      if (j < width) {
+        ed[j] = __ldcs(sedge + base + (int64_t)j * 32);
+        cf[j] = __ldcs(scoef + base + (int64_t)j * 32);
+      }
+    for (int64_t k0 = 0; k0 < width; k0 += B) {
+      // gathers of this batch, then the plan of the next one, then the adds:
+      // one memory round trip per batch instead of two
+      double av[B];
 #pragma unroll
       for (int j = 0; j < B; ++j)
         if (k0 + j < width) av[j] = a_val[ed[j]];
+      int edn[B];
+      double cfn[B];
+#pragma unroll
+      for (int j = 0; j < B; ++j)
+        if (k0 + B + j < width) {
+          edn[j] = __ldcs(sedge + base + (k0 + B + j) * 32);
+          cfn[j] = __ldcs(scoef + base + (k0 + B + j) * 32);
+        }
 #pragma unroll
       for (int j = 0; j < B; ++j)
         if (k0 + j < width) acc = __fma_rn(cf[j], av[j], acc);
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        ed[j] = edn[j];
+        cf[j] = cfn[j];
+      }
     }
     emit_entry(up_entry[i], mirror[i], acc, c_val, csr2ell, e64, e32, d64, d32, di64, di32, err);
   }
