@@ -111,15 +111,17 @@ __global__ void __launch_bounds__(256) k_gs_m(int64_t s0, int64_t s1, const int6
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, part = warp % G;
   const int64_t s = s0 + (int64_t)blockIdx.x * (8 / G) + warp / G;
   const MRow m = m_row<G>(s, s1, ptr, row0, nrow, part, lane);
-  float acc[NR];
+  float acc[NR], bv[NR];
 #pragma unroll
-  for (int c = 0; c < NR; ++c) acc[c] = 0.f;
+  for (int c = 0; c < NR; ++c) acc[c] = bv[c] = 0.f;
+  float d = 0.f;
+  if (part == 0 && m.active) {  // issued with the gathers, not after the combining barrier
+    load_row<NR>(B + m.r * NR, bv);
+    d = dinv[m.r];
+  }
   m_dot<NR, G>(m, col, val, X, acc);  // other colours: not written by this launch
   m_combine<NR, G>(acc, warp, lane);
   if (part == 0 && m.active) {
-    float bv[NR];
-    load_row<NR>(B + m.r * NR, bv);
-    const float d = dinv[m.r];
 #pragma unroll
     for (int c = 0; c < NR; ++c) acc[c] = (bv[c] - acc[c]) * d;
     store_row<NR>(X + m.r * NR, acc);
@@ -136,12 +138,13 @@ __global__ void __launch_bounds__(256) k_residual_m(int64_t nslice, const int64_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, part = warp % G;
   const int64_t s = (int64_t)blockIdx.x * (8 / G) + warp / G;
   const MRow m = m_row<G>(s, nslice, ptr, row0, nrow, part, lane);
-  float acc[NR];
+  float acc[NR], bv[NR];
 #pragma unroll
-  for (int c = 0; c < NR; ++c) acc[c] = 0.f;
+  for (int c = 0; c < NR; ++c) acc[c] = bv[c] = 0.f;
   if (part == 0 && m.active) {
     float xv[NR];
     load_row<NR>(X + m.r * NR, xv);
+    load_row<NR>(B + m.r * NR, bv);  // issued with the gathers, not after the combining barrier
     const float d = diag[m.r];
 #pragma unroll
     for (int c = 0; c < NR; ++c) acc[c] = d * xv[c];
@@ -149,8 +152,6 @@ __global__ void __launch_bounds__(256) k_residual_m(int64_t nslice, const int64_
   m_dot<NR, G>(m, col, val, X, acc);
   m_combine<NR, G>(acc, warp, lane);
   if (part == 0 && m.active) {
-    float bv[NR];
-    load_row<NR>(B + m.r * NR, bv);
 #pragma unroll
     for (int c = 0; c < NR; ++c) acc[c] = bv[c] - acc[c];
     store_row<NR>(R + m.r * NR, acc);

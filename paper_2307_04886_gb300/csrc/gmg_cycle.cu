@@ -161,9 +161,12 @@ __global__ void __launch_bounds__(256, (G == 1 && sizeof(T) == 4) ? 8 : 1) k_gs(
   const T di = (part == 0 && p.active) ? dinv[p.row] : T(0);
   pdl_wait();
   pdl_trigger();
+  // b is issued with the gathers: after the barrier of combine_parts its load
+  // would be one more dependent round trip to L2
+  const T bv = (part == 0 && p.active) ? b[p.row] : T(0);
   T acc = row_dot<T, G>(p, pv, pc, col, val, x);
   acc = combine_parts<T, G>(acc, warp, lane);
-  if (part == 0 && p.active) x[p.row] = (b[p.row] - acc) * di;
+  if (part == 0 && p.active) x[p.row] = (bv - acc) * di;
 }
 
 // r = b - A x over all slices; with `partial`, per-block sums of r^2.
@@ -182,11 +185,13 @@ __global__ void __launch_bounds__(256) k_residual(int64_t nslice, const int64_t*
   const T d = (part == 0 && p.active) ? diag[p.row] : T(0);
   pdl_wait();
   pdl_trigger();
+  const bool own = part == 0 && p.active;
+  const T bv = own ? b[p.row] : T(0), xv = own ? x[p.row] : T(0);  // issued with the gathers
   T acc = row_dot<T, G>(p, pv, pc, col, val, x);
   acc = combine_parts<T, G>(acc, warp, lane);
   double sq = 0.0;
-  if (part == 0 && p.active) {
-    const T rv = b[p.row] - (acc + d * x[p.row]);
+  if (own) {
+    const T rv = bv - (acc + d * xv);
     r[p.row] = rv;
     sq = (double)rv * (double)rv;
   }
@@ -251,6 +256,8 @@ __global__ void __launch_bounds__(256) k_restrict(int64_t nslice, const int64_t*
   T pv[kPrefetch];
   int pc[kPrefetch];
   prefetch_row<T, 1>(p, col, w, pv, pc);
+  const bool c0 = p.active && p.row < nc0;
+  const T dc = c0 ? dinvc[p.row] : T(0);
   pdl_wait();
   pdl_trigger();
   if (!p.active) return;
@@ -258,7 +265,7 @@ __global__ void __launch_bounds__(256) k_restrict(int64_t nslice, const int64_t*
   bc[p.row] = acc;
   // the first Gauss-Seidel colour of the coarse pre-smoothing from x = 0:
   // (b - 0) / a_ii for the rows of colour 0 (the first nc0 rows)
-  xc[p.row] = p.row < nc0 ? (acc - T(0)) * dinvc[p.row] : T(0);
+  xc[p.row] = c0 ? (acc - T(0)) * dc : T(0);
 }
 
 // x += P u (three packed slots per fine row).
