@@ -246,7 +246,8 @@ struct gmg_ctx {
   double* dense = nullptr;  // npad x npad sweep work matrix (npad = n rounded up to 32)
   double* Ainv = nullptr;   // A_lambda^-1 (symmetric, full, n x n)
   double* dbuf = nullptr;   // two 32 x 32 pivot inverses, panel U and U D^-1 (npad x 32 each)
-  int* gj_cnt = nullptr;    // per-sweep arrival counters of the next pivot tile
+  int* gj_cnt = nullptr;    // per sweep: arrival counter of the next pivot tile, then work counter
+  int nsm = 1;              // SMs of the device (persistent grids)
   // A(t) = M + t L kept split (gmg_setup_ML): lumped mass, L values (caller
   // CSR order), position of every row's diagonal entry
   double* ml_M = nullptr;

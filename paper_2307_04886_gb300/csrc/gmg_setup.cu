@@ -564,18 +564,38 @@ __device__ __forceinline__ double sym_at(const double* S, int ld, int i, int j) 
   return i >= j ? S[(int64_t)i * ld + j] : S[(int64_t)j * ld + i];
 }
 
-// 1 / d by Newton-Raphson iteration r <- r (2 - d r), written as
-// e = 1 - d r, r <- r + r e, from the FP32 reciprocal (about 2^-23 relative
-// error; two steps reach the FP64 rounding level).  Values outside the FP32
-// range use the FP64 division.
+// 1 / d from an FP32 seed r0 (relative error e0 = 1 - d r0 of about
+// 2^-22) and one step of the cubic Newton-Raphson iteration
+// r = r0 (1 + e0 + e0^2), whose truncation error is e0^3 (about 2^-66): the
+// result is within one unit in the last place.  The seed's conversions are
+// done on the bits with integer operations (the FP32 value is d's exponent
+// and leading 23 mantissa bits, the seed widens exactly), because on this
+// GPU a conversion between FP64 and FP32 costs about 96 cycles and an FP64
+// fused multiply-add 64 cycles per warp instruction, and this reciprocal is
+// on the dependent path of every pivot of the coarsest inverse.  |d| outside
+// [2^-100, 2^100] uses the FP64 division.
 __device__ __forceinline__ double recip_newton(double d) {
-  const float f = (float)d;
-  if (!(fabsf(f) >= 1e-30f && fabsf(f) <= 1e30f)) return 1.0 / d;
-  double r = (double)__frcp_rn(f);
-  double e = __fma_rn(-d, r, 1.0);
-  r = __fma_rn(r, e, r);
-  e = __fma_rn(-d, r, 1.0);
-  return __fma_rn(r, e, r);
+  const long long bits = __double_as_longlong(d);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  if (ex < 1023 - 100 || ex > 1023 + 100) return 1.0 / d;
+  const unsigned fb = ((unsigned)((unsigned long long)bits >> 32) & 0x80000000u) | ((unsigned)(ex - 1023 + 127) << 23) |
+                      ((unsigned)(bits >> 29) & 0x7FFFFFu);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(fb)));
+  const unsigned rb = __float_as_uint(rf);
+  const long long r0b = ((long long)(rb & 0x80000000u) << 32) |
+                        ((long long)((int)((rb >> 23) & 0xFFu) - 127 + 1023) << 52) | ((long long)(rb & 0x7FFFFFu) << 29);
+  const double r0 = __longlong_as_double(r0b);
+  const double e0 = __fma_rn(-d, r0, 1.0);
+  const double t = __fma_rn(e0, e0, e0);
+  return __fma_rn(r0, t, r0);
+}
+
+// A pivot usable by the sweep: positive, finite (a test on the bits: an FP64
+// comparison sits on the dependent path, an integer one is a few cycles).
+__device__ __forceinline__ bool pivot_ok(double d) {
+  const long long b = __double_as_longlong(d);
+  return b > 0 && b < 0x7FF0000000000000LL;
 }
 
 // m <- m^-1 for a 32 x 32 SPD block held in both triangles, by 32 scalar
@@ -604,7 +624,7 @@ __device__ void sweep_inverse32(double (&m)[32][33], int* bad) {
   // step 0's pivot and column
   if (warp == 0) {
     double d = m[0][0];
-    if (!(d > 0.0)) {
+    if (!pivot_ok(d)) {
       if (lane == 0) *bad = 1;
       d = 1.0;
     }
@@ -628,7 +648,7 @@ __device__ void sweep_inverse32(double (&m)[32][33], int* bad) {
           v = __fma_rn(-ck[cur][a], cs[cur][bb], m[a][bb]);
         m[a][bb] = v;
         double d = __shfl_sync(0xffffffffu, v, kp);
-        if (!(d > 0.0)) {
+        if (!pivot_ok(d)) {
           if (lane == 0) *bad = 1;
           d = 1.0;
         }
@@ -725,65 +745,125 @@ __device__ __forceinline__ void lower_tile(int t, int first, int nbk, int* I, in
   *I = j + t;
 }
 
-// Update of sweep P, one CTA per 8-row quarter of a lower tile.  The four
-// quarters of the next pivot tile (P+1, P+1) come first; the last of them to
-// finish (arrival counter cnt[P]) inverts that tile into DinvNext.
-__global__ void __launch_bounds__(256) k_gj_update(int npad, int P, double* __restrict__ S,
-                                                   const double* __restrict__ Dinv, const double* __restrict__ Uo,
-                                                   const double* __restrict__ Uh, int* __restrict__ cnt,
-                                                   double* __restrict__ DinvNext, int* __restrict__ status) {
-  __shared__ double uo[32][33], uh[8][33];
-  __shared__ double m[32][33];
-  __shared__ int last, bad;
-  pdl_wait();
-  pdl_trigger();
-  const int nbk = npad / 32;
-  const int tid = threadIdx.x, rr = tid >> 5, cc = tid & 31;
-  const int q = blockIdx.x & 3, tt = blockIdx.x >> 2;
-  const bool has_next = P + 1 < nbk;
+// Quarter `it` of the work list of sweep P: tile (I, J) (the next pivot tile
+// first, then lower_tile order) and its quarter q.
+__device__ __forceinline__ void gj_item(int it, int P, int nbk, int* I, int* J, int* q) {
+  *q = it & 3;
+  const int tt = it >> 2;
   int t = tt;
-  if (has_next) {  // move the next pivot tile to the front of the order
+  if (P + 1 < nbk) {
     const int tD = (P + 1) * nbk - P * (P + 1) / 2;  // lower_tile index of (P+1, P+1)
     t = tt == 0 ? tD : (tt <= tD ? tt - 1 : tt);
   }
-  int I, J;
-  lower_tile(t, 0, nbk, &I, &J);
-  const int r = I * 32 + q * 8 + rr, c = J * 32 + cc;
-  double* out = S + (int64_t)r * npad + c;
-  if (I == P && J == P) {
-    *out = -Dinv[(r - P * 32) * 32 + cc];
-  } else if (J == P) {
-    *out = Uh[(int64_t)r * 32 + cc];
-  } else if (I == P) {
-    *out = Uh[(int64_t)c * 32 + (r - P * 32)];
-  } else {
-    for (int e = tid; e < 1024; e += 256) uo[e >> 5][e & 31] = Uo[(int64_t)(J * 32 + (e >> 5)) * 32 + (e & 31)];
-    uh[rr][cc] = Uh[(int64_t)r * 32 + cc];
+  lower_tile(t, 0, nbk, I, J);
+}
+
+// Update of sweep P over the 8-row quarters of every lower tile, taken from a
+// work counter (work[P]) by a persistent grid of about one CTA per SM; each
+// CTA claims its next quarter and loads that quarter's operands into
+// registers while it computes the current one.  The four quarters of the
+// next pivot tile (P+1, P+1) come first; the CTA that finishes the last of
+// them (arrival counter cnt[P]) inverts that tile into DinvNext and takes no
+// more quarters, so the 32 dependent pivot steps of the inversion run on an
+// SM of their own: an SM's FP64 pipe is shared by its warps (a warp's FP64
+// instruction occupies its sub-partition's pipe for 64 cycles), and with the
+// whole update resident at once the inversion used to wait behind the
+// quarters placed on its SM.
+__global__ void __launch_bounds__(256) k_gj_update(int npad, int P, double* __restrict__ S,
+                                                   const double* __restrict__ Dinv, const double* __restrict__ Uo,
+                                                   const double* __restrict__ Uh, int* __restrict__ cnt,
+                                                   int* __restrict__ work, double* __restrict__ DinvNext,
+                                                   int* __restrict__ status) {
+  __shared__ double uo[32][33], uh[8][33];
+  __shared__ double m[32][33];
+  __shared__ int last, bad, item;
+  pdl_wait();
+  pdl_trigger();
+  const int nbk = npad / 32;
+  const int nitems = 4 * nbk * (nbk + 1) / 2;
+  const int tid = threadIdx.x, rr = tid >> 5, cc = tid & 31;
+  const bool has_next = P + 1 < nbk;
+  double ruo[4], ruh = 0.0;
+  // operands of a bulk quarter (neither index on the pivot block P) into registers
+  auto fetch = [&](int it) {
+    if (it >= nitems) return;
+    int I, J, q;
+    gj_item(it, P, nbk, &I, &J, &q);
+    if (I == P || J == P) return;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u;
+      ruo[u] = Uo[(int64_t)(J * 32 + (e >> 5)) * 32 + (e & 31)];
+    }
+    ruh = Uh[(int64_t)(I * 32 + q * 8 + rr) * 32 + cc];
+  };
+  if (tid == 0) item = atomicAdd(work + P, 1);
+  __syncthreads();
+  int cur = item;
+  __syncthreads();
+  fetch(cur);
+  while (cur < nitems) {
+    int I, J, q;
+    gj_item(cur, P, nbk, &I, &J, &q);
+    // a quarter of the next pivot tile may end with this CTA inverting it:
+    // its successor is claimed only after the arrival test
+    const bool pivq = has_next && I == P + 1 && J == P + 1;
+    const bool bulk = I != P && J != P;
+    if (!pivq && tid == 0) item = atomicAdd(work + P, 1);
+    if (bulk) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = tid + 256 * u;
+        uo[e >> 5][e & 31] = ruo[u];
+      }
+      uh[rr][cc] = ruh;
+    }
     __syncthreads();
-    double acc = 0.0;
+    int nxt = pivq ? nitems : item;
+    if (!pivq) fetch(nxt);
+    const int r = I * 32 + q * 8 + rr, c = J * 32 + cc;
+    double* out = S + (int64_t)r * npad + c;
+    if (I == P && J == P) {
+      *out = -Dinv[(r - P * 32) * 32 + cc];
+    } else if (J == P) {
+      *out = Uh[(int64_t)r * 32 + cc];
+    } else if (I == P) {
+      *out = Uh[(int64_t)c * 32 + (r - P * 32)];
+    } else {
+      double acc = 0.0;
 #pragma unroll 8
-    for (int k = 0; k < 32; ++k) acc += uh[rr][k] * uo[cc][k];
-    *out -= acc;
+      for (int k = 0; k < 32; ++k) acc += uh[rr][k] * uo[cc][k];
+      *out -= acc;
+    }
+    if (pivq) {
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) {
+        last = atomicAdd(cnt + P, 1) == 3;
+        bad = 0;
+      }
+      __syncthreads();
+      if (last) {
+        __threadfence();
+        const double* T = S + (int64_t)(P + 1) * 32 * npad + (P + 1) * 32;
+        for (int e = tid; e < 1024; e += 256) {
+          const int i = e >> 5, j = e & 31;
+          m[i][j] = __ldcg(T + (int64_t)(i >= j ? i : j) * npad + (i >= j ? j : i));
+        }
+        __syncthreads();
+        sweep_inverse32(m, &bad);
+        for (int e = tid; e < 1024; e += 256) DinvNext[e] = m[e >> 5][e & 31];
+        if (tid == 0 && bad) atomicOr(status, 1);
+        return;
+      }
+      if (tid == 0) item = atomicAdd(work + P, 1);
+      __syncthreads();
+      nxt = item;
+      fetch(nxt);
+    }
+    __syncthreads();  // the tile in shared memory and `item` are reused
+    cur = nxt;
   }
-  if (!has_next || I != P + 1 || J != P + 1) return;
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    last = atomicAdd(cnt + P, 1) == 3;
-    bad = 0;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  const double* T = S + (int64_t)(P + 1) * 32 * npad + (P + 1) * 32;
-  for (int e = tid; e < 1024; e += 256) {
-    const int i = e >> 5, j = e & 31;
-    m[i][j] = __ldcg(T + (int64_t)(i >= j ? i : j) * npad + (i >= j ? j : i));
-  }
-  __syncthreads();
-  sweep_inverse32(m, &bad);
-  for (int e = tid; e < 1024; e += 256) DinvNext[e] = m[e >> 5][e & 31];
-  if (tid == 0 && bad) atomicOr(status, 1);
 }
 
 // Ainv = -S (both triangles, leading dimension n), and its FP32 copy.
@@ -1340,7 +1420,7 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s, bool defer) {
   double* Dinv[2] = {c->dbuf, c->dbuf + 1024};
   double* Uo = c->dbuf + 2048;
   double* Uh = Uo + (size_t)npad * 32;
-  GMG_CK(cudaMemsetAsync(c->gj_cnt, 0, sizeof(int) * (size_t)nbk, s));
+  GMG_CK(cudaMemsetAsync(c->gj_cnt, 0, sizeof(int) * (size_t)(2 * nbk), s));  // arrival and work counters
   k_gj_pad<<<grid_for((int64_t)npad * npad, 256), 256, 0, s>>>(npad, n, c->dense);
   GMG_LAUNCHED();
   k_csr_to_dense<<<std::min(n, 4096), 128, 0, s>>>(n, npad, C.csr_rowptr, C.csr_col, C.csr_val, C.iperm, c->dense);
@@ -1349,9 +1429,9 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s, bool defer) {
   for (int p = 0; p < nbk; ++p) {
     GMG_TRY(launch(k_gj_panel, npad / 8, 256, s, npad, p, (const double*)c->dense, (const double*)Dinv[p & 1], Uo,
                    Uh));
-    GMG_TRY(launch(k_gj_update, (int64_t)4 * nbk * (nbk + 1) / 2, 256, s, npad, p, c->dense,
-                   (const double*)Dinv[p & 1], (const double*)Uo, (const double*)Uh, c->gj_cnt, Dinv[(p + 1) & 1],
-                   c->dstatus + 1));
+    GMG_TRY(launch(k_gj_update, std::min<int64_t>(c->nsm, (int64_t)4 * nbk * (nbk + 1) / 2), 256, s, npad, p,
+                   c->dense, (const double*)Dinv[p & 1], (const double*)Uo, (const double*)Uh, c->gj_cnt,
+                   c->gj_cnt + nbk, Dinv[(p + 1) & 1], c->dstatus + 1));
   }
   GMG_TRY(launch(k_gj_finish, grid_for((int64_t)n * n, 256), 256, s, n, npad, (const double*)c->dense, c->Ainv,
                  c->Ainv32));
@@ -1615,6 +1695,7 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
                       cudaStream_t s) {
   GMG_TRY(validate(A, nP, P, coloring));
   GMG_CK(cudaGetDevice(&c->device));
+  GMG_CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
   Arena& a = c->arena;
   c->nlev = nP + 1;
   c->L.resize(c->nlev);
@@ -1674,7 +1755,7 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
     GMG_TRY(a.alloc(&c->Ainv, (size_t)(c->nco * c->nco)));
     GMG_TRY(a.alloc(&c->Ainv32, (size_t)(c->nco * c->nco)));
     GMG_TRY(a.alloc(&c->dbuf, (size_t)(2048 + 64 * npad)));  // two pivot inverses, panel U and U D^-1
-    GMG_TRY(a.alloc(&c->gj_cnt, (size_t)nbk));
+    GMG_TRY(a.alloc(&c->gj_cnt, (size_t)(2 * nbk)));
   }
   // outer-iteration vectors
   const int64_t n = L0.n;

@@ -446,9 +446,9 @@ def test_many_meshes_one_iteration_matches_oracle(gmg):
 def test_pivot_reciprocal_within_one_ulp(gmg):
     """The Newton-Raphson reciprocal used for every pivot of the coarsest
     inverse against the correctly rounded division 1.0 / d: a log-spaced sweep
-    over [1e-30, 1e30], values next to powers of two and the FP32-range edges
-    (where the FP64 division takes over) stay within one unit in the last
-    place."""
+    over [1e-30, 1e30], values next to powers of two, the edges of the seeded
+    range [2^-100, 2^101) and values beyond them (where the FP64 division
+    takes over) stay within one unit in the last place."""
     import torch
 
     d = np.concatenate([
@@ -457,6 +457,8 @@ def test_pivot_reciprocal_within_one_ulp(gmg):
         np.ldexp(1.0, np.arange(-99, 100)) * (1 - 2.0**-53),
         np.random.default_rng(5).uniform(0.5, 2.0, 20000),
         np.array([1e-30, 1e30, 9.99e-31, 1.001e30, 3.0, 7.0, 1.0 / 3.0, np.pi]),
+        np.array([np.ldexp(1.0, -100), np.ldexp(1.0, -100) * (1 - 2.0**-53), np.ldexp(1.0, 101) * (1 - 2.0**-53),
+                  np.ldexp(1.0, 101), 1e-35, 1e35, 1e-300, 1e300, 1.7e308]),
     ])
     dd = torch.tensor(d, device="cuda")
     out = torch.empty_like(dd)
