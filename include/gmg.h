@@ -130,8 +130,10 @@ const char *gmg_last_error(void);
  *
  * `coloring` selects the Gauss-Seidel colouring of Sec. 3's relaxation: NULL,
  * or an array of n_prolong + 1 host pointers, one per level, each NULL (that
- * level gets the library's greedy first-fit colouring in increasing row
- * index) or n_l colours in [0, n_l) in the caller's numbering of level l.  No
+ * level gets the library's deterministic colouring: greedy first fit in
+ * increasing row index and in smallest-last order, each improved by eight
+ * iterated-greedy passes, the one with fewer colours kept) or n_l colours in
+ * [0, n_l) in the caller's numbering of level l.  No
  * two adjacent rows of A_l (a stored off-diagonal entry) may share a colour;
  * pre-relaxation visits the colours in ascending order, post-relaxation in
  * descending order.  The coarse levels are numbered as the columns of P_l, and
@@ -148,14 +150,22 @@ gmg_status gmg_setup(gmg_handle *h, const gmg_csr *A, int n_prolong, const gmg_p
 
 /* Numeric refresh: new values for A on the SAME sparsity pattern (`val` has
  * rowptr[n] entries in the pattern's order; host or device per `mem`).
- * Recomputes every Galerkin level and the coarsest factor on the GPU without
- * touching the host-side structure.  Errors: NOT_SPD, CHOLESKY, NONFINITE. */
+ * Recomputes every Galerkin level on the GPU without touching the host-side
+ * structure, checks them before returning, and starts the coarsest inverse
+ * on a stream of the handle's own, ordered after the Galerkin values on
+ * `stream`.  The next call on the handle that needs the inverse (gmg_solve,
+ * gmg_solve_batched, gmg_vcycle, gmg_vcycle_batched, gmg_coarse_solve, or
+ * another refresh) makes its own stream wait for it (a CG solve only right
+ * before its first coarsest solve, so the first cycle's descent overlaps
+ * it) and reports a non-positive pivot of it as CHOLESKY.
+ * Errors: NOT_SPD, NONFINITE (this call); CHOLESKY (the next such call). */
 gmg_status gmg_set_values(gmg_handle h, const double *val, int mem, void *stream);
 
 /* Alg. 1 iteration: solves A x = b to ||b - A x||_2 <= tol ||b||_2.  `x` holds
  * the initial guess on entry and the solution on exit (n doubles, host or
  * device per `mem`).  b == 0 gives x = 0 after 0 iterations.  `info` may be
- * NULL.  Errors: NOT_CONVERGED (x = last iterate), NONFINITE, INVALID_ARG. */
+ * NULL.  Errors: NOT_CONVERGED (x = last iterate), NONFINITE, INVALID_ARG,
+ * CHOLESKY (the coarsest inverse of a preceding refresh). */
 gmg_status gmg_solve(gmg_handle h, const double *b, double *x, double tol, int mem, gmg_solve_info *info,
                      void *stream);
 
@@ -184,7 +194,8 @@ gmg_status gmg_setup_ML(gmg_handle *h, const double *M_diag, const gmg_csr *L, d
                         void *stream);
 
 /* Numeric refresh for a new t: A_1 = M + t L on the GPU, then every
- * Galerkin level and the coarsest factor (as gmg_set_values). */
+ * Galerkin level and the coarsest inverse (as gmg_set_values, with the same
+ * overlap of the inverse and the same errors). */
 gmg_status gmg_set_t(gmg_handle h, double t, void *stream);
 
 /* out = M u (device vectors, caller numbering): the right-hand side M u0 of
@@ -377,12 +388,22 @@ gmg_status gmg_vcycle(gmg_handle h, int fp32, const double *b, double *x, void *
 gmg_status gmg_vcycle_batched(gmg_handle h, int nrhs, const double *B, double *X, void *stream);
 
 /* The reciprocal 1/d that the coarsest inverse (Alg. 2's direct solve) takes
- * of each pivot: Newton-Raphson iteration r <- r + r (1 - d r) from the FP32
- * reciprocal, two steps.  Applied elementwise to n device values d (out: n
- * device values); exposed so that it can be checked against the correctly
- * rounded division.  Values outside [1e-30, 1e30] in magnitude take the FP64
- * division. */
+ * of each pivot, and the set-up of every level of 1/a_ii: from an FP32 seed
+ * built from d's bits, one cubic Newton-Raphson step r0 (1 + e + e^2),
+ * e = 1 - d r0.  Applied elementwise to n device values d (out: n device
+ * values); exposed so that it can be checked against the correctly rounded
+ * division (within one unit in the last place).  Values outside
+ * [2^-100, 2^101) in magnitude take the FP64 division.
+ * Errors: INVALID_ARG (n < 0, or a null pointer with n > 0). */
 gmg_status gmg_pivot_reciprocal(int64_t n, const double *d, double *out, void *stream);
+
+/* The precision conversions of the solver's kernels, done on the IEEE 754
+ * bit patterns with integer operations: dir 0 narrows n device doubles `in`
+ * to floats `out` (round to nearest even), dir 1 widens n device floats to
+ * doubles (exact).  Exposed so that they can be checked against the IEEE 754
+ * conversions.  Errors: INVALID_ARG (n < 0, dir not 0 or 1, or a null
+ * pointer with n > 0). */
+gmg_status gmg_convert(int64_t n, int dir, const void *in, void *out, void *stream);
 
 /* ---- allocation-free residual (no counterpart in the paper) ----
  * For callers that cannot allocate device memory (code running inside

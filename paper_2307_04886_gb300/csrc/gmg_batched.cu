@@ -213,14 +213,14 @@ __global__ void __launch_bounds__(256) k_coarse_m(int n, const double* __restric
   for (int j = lane; j < n; j += 32) {
     const double aj = a[j];
 #pragma unroll
-    for (int c = 0; c < NR; ++c) s[c] += aj * (double)B[(int64_t)j * NR + c];
+    for (int c = 0; c < NR; ++c) s[c] += aj * f64_of(B[(int64_t)j * NR + c]);
   }
 #pragma unroll
   for (int c = 0; c < NR; ++c)
     for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
   if (lane == 0)
 #pragma unroll
-    for (int c = 0; c < NR; ++c) X[(int64_t)row * NR + c] = (float)s[c];
+    for (int c = 0; c < NR; ++c) X[(int64_t)row * NR + c] = f32_rn(s[c]);
 }
 
 // FP64 outer residual R = B - A X with per-block, per-column partial sums of
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(256) k_outer_residual_m(int64_t nslice, const 
 #pragma unroll
     for (int c = 0; c < NR; ++c) {
       const double rv = B[r * NR + c] - acc[c];
-      R32[r * NR + c] = (float)rv;
+      R32[r * NR + c] = f32_rn(rv);
       sq[c] = rv * rv;
     }
   }
@@ -315,7 +315,7 @@ __global__ void k_zero_cols(int64_t n, int NR, int mask, double* __restrict__ X)
 }
 __global__ void k_add_f2d_m(int64_t m, const float* __restrict__ e, double* __restrict__ x) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += (double)e[i];
+    x[i] += f64_of(e[i]);
 }
 
 static inline int nblk(int64_t threads) { return (int)std::max<int64_t>(1, (threads + 255) / 256); }

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) k_residual(int64_t nslice, const int64_t*
   if (own) {
     const T rv = bv - (acc + d * xv);
     r[p.row] = rv;
-    sq = (double)rv * (double)rv;
+    sq = to_f64(rv) * to_f64(rv);
   }
   if (partial) {  // fixed-shape block reduction of r^2
     __shared__ double red[256];
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256) k_coarse(int n, const double* __restrict_
   if (row >= n) return;
   const double* a = Ainv + (int64_t)row * n;
   double s = 0.0;
-  for (int j = lane; j < n; j += 32) s += a[j] * (double)b[j];
+  for (int j = lane; j < n; j += 32) s += a[j] * to_f64(b[j]);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) x[row] = (T)s;
 }
@@ -319,7 +319,7 @@ __global__ void k_scatter_vec(int64_t n, const int32_t* __restrict__ perm, const
 __global__ void k_d2f(int64_t n, const double* a, float* b) {
   pdl_wait();
   pdl_trigger();
-  GRID_LOOP(i, n) b[i] = (float)a[i];
+  GRID_LOOP(i, n) b[i] = f32_rn(a[i]);
 }
 // b32 = (float) r and x32 = 0: the right-hand side and zero initial guess of
 // a correction cycle MGI(0, r); the rows of colour 0 (the first n0) take
@@ -329,7 +329,7 @@ __global__ void k_d2f_zero(int64_t n, const double* r, float* b32, float* x32, c
   pdl_wait();
   pdl_trigger();
   GRID_LOOP(i, n) {
-    const float bi = (float)r[i];
+    const float bi = f32_rn(r[i]);
     b32[i] = bi;
     x32[i] = i < n0 ? (bi - 0.f) * dinv32[i] : 0.f;
   }
@@ -337,13 +337,13 @@ __global__ void k_d2f_zero(int64_t n, const double* r, float* b32, float* x32, c
 __global__ void k_f2d(int64_t n, const float* a, double* b) {
   pdl_wait();
   pdl_trigger();
-  GRID_LOOP(i, n) b[i] = (double)a[i];
+  GRID_LOOP(i, n) b[i] = f64_of(a[i]);
 }
 // x += (double) e
 __global__ void k_add_f2d(int64_t n, const float* e, double* x) {
   pdl_wait();
   pdl_trigger();
-  GRID_LOOP(i, n) x[i] += (double)e[i];
+  GRID_LOOP(i, n) x[i] += f64_of(e[i]);
 }
 
 // Deterministic dot product: fixed grid, fixed per-thread ranges, fixed tree.
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(256) k_pcg_axpy(int64_t n, double* sc, const d
     const double rn = ri - alpha * q[i];
     r[i] = rn;
     if constexpr (sizeof(Z) == 4) {
-      const float bi = (float)rn;
+      const float bi = f32_rn(rn);
       b32[i] = bi;
       z0[i] = i < n0 ? (bi - 0.f) * dinv[i] : 0.f;
     } else {
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(256) k_pcg_zdots(int64_t n, const Z* __restric
   double num = 0.0, rz = 0.0;
 #pragma unroll 4
   for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
-    const double zi = (double)z[i], ri = r[i];
+    const double zi = to_f64(z[i]), ri = r[i];
     num += zi * (ri - rold[i]);
     rz += ri * zi;
   }
@@ -485,7 +485,7 @@ __global__ void k_pcg_dir(int64_t n, const double* sc, const Z* __restrict__ z, 
   pdl_wait();
   pdl_trigger();
   const double beta = sc[S_BETA];
-  GRID_LOOP(i, n) p[i] = (double)z[i] + beta * p[i];
+  GRID_LOOP(i, n) p[i] = to_f64(z[i]) + beta * p[i];
 }
 // z = 0 with the rows of colour 0 (the first n0) at their first Gauss-Seidel
 // update from zero, (r - 0) / a_ii: the start of an FP64 correction cycle

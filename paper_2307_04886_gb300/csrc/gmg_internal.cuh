@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "gmg.h"
+#include "gmg_fpbits.cuh"
 
 namespace gmg {
 

@@ -409,25 +409,27 @@ __device__ __forceinline__ void emit_entry(int64_t e, int64_t m, double x, doubl
                                            float* __restrict__ e32, double* __restrict__ d64,
                                            float* __restrict__ d32, double* __restrict__ di64,
                                            float* __restrict__ di32, int* __restrict__ err) {
-  if (!isfinite(x)) atomicOr(err, 2);
+  if (!finite_bits(x)) atomicOr(err, 2);
   c_val[e] = x;
   const int64_t se = csr2ell[e];
+  const float x32 = f32_rn(x);
   if (se >= 0) {
     e64[se] = x;
-    e32[se] = (float)x;
+    e32[se] = x32;
   } else {
     const int64_t r = -1 - se;
-    if (!(x > 0.0)) atomicOr(err, 1);
+    if (!positive_bits(x)) atomicOr(err, 1);
+    const double xi = recip_newton(x);
     d64[r] = x;
-    d32[r] = (float)x;
-    di64[r] = 1.0 / x;
-    di32[r] = (float)(1.0 / x);
+    d32[r] = x32;
+    di64[r] = xi;
+    di32[r] = f32_rn(xi);
   }
   if (m >= 0) {
     c_val[m] = x;
     const int64_t sm = csr2ell[m];
     e64[sm] = x;
-    e32[sm] = (float)x;
+    e32[sm] = x32;
   }
 }
 
@@ -518,16 +520,17 @@ __global__ void k_scatter_rows(int64_t nslice, const int64_t* __restrict__ ptr, 
     int64_t slot = ptr[sl] + lane;
     for (int64_t e = rp[old], e1 = rp[old + 1]; e < e1; ++e) {
       const double x = v[e];
-      if (!isfinite(x)) atomicOr(err, 2);
+      if (!finite_bits(x)) atomicOr(err, 2);
       if (ci[e] == old) {
-        if (!(x > 0.0)) atomicOr(err, 1);
+        if (!positive_bits(x)) atomicOr(err, 1);
+        const double xi = recip_newton(x);
         d64[r] = x;
-        d32[r] = (float)x;
-        di64[r] = 1.0 / x;
-        di32[r] = (float)(1.0 / x);
+        d32[r] = f32_rn(x);
+        di64[r] = xi;
+        di32[r] = f32_rn(xi);
       } else {
         e64[slot] = x;
-        e32[slot] = (float)x;
+        e32[slot] = f32_rn(x);
         slot += 32;
       }
     }
@@ -564,40 +567,6 @@ __device__ __forceinline__ double sym_at(const double* S, int ld, int i, int j) 
   return i >= j ? S[(int64_t)i * ld + j] : S[(int64_t)j * ld + i];
 }
 
-// 1 / d from an FP32 seed r0 (relative error e0 = 1 - d r0 of about
-// 2^-22) and one step of the cubic Newton-Raphson iteration
-// r = r0 (1 + e0 + e0^2), whose truncation error is e0^3 (about 2^-66): the
-// result is within one unit in the last place.  The seed's conversions are
-// done on the bits with integer operations (the FP32 value is d's exponent
-// and leading 23 mantissa bits, the seed widens exactly), because on this
-// GPU a conversion between FP64 and FP32 costs about 96 cycles and an FP64
-// fused multiply-add 64 cycles per warp instruction, and this reciprocal is
-// on the dependent path of every pivot of the coarsest inverse.  |d| outside
-// [2^-100, 2^100] uses the FP64 division.
-__device__ __forceinline__ double recip_newton(double d) {
-  const long long bits = __double_as_longlong(d);
-  const int ex = (int)((bits >> 52) & 0x7FF);
-  if (ex < 1023 - 100 || ex > 1023 + 100) return 1.0 / d;
-  const unsigned fb = ((unsigned)((unsigned long long)bits >> 32) & 0x80000000u) | ((unsigned)(ex - 1023 + 127) << 23) |
-                      ((unsigned)(bits >> 29) & 0x7FFFFFu);
-  float rf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(fb)));
-  const unsigned rb = __float_as_uint(rf);
-  const long long r0b = ((long long)(rb & 0x80000000u) << 32) |
-                        ((long long)((int)((rb >> 23) & 0xFFu) - 127 + 1023) << 52) | ((long long)(rb & 0x7FFFFFu) << 29);
-  const double r0 = __longlong_as_double(r0b);
-  const double e0 = __fma_rn(-d, r0, 1.0);
-  const double t = __fma_rn(e0, e0, e0);
-  return __fma_rn(r0, t, r0);
-}
-
-// A pivot usable by the sweep: positive, finite (a test on the bits: an FP64
-// comparison sits on the dependent path, an integer one is a few cycles).
-__device__ __forceinline__ bool pivot_ok(double d) {
-  const long long b = __double_as_longlong(d);
-  return b > 0 && b < 0x7FF0000000000000LL;
-}
-
 // m <- m^-1 for a 32 x 32 SPD block held in both triangles, by 32 scalar
 // sweeps of its lower triangle, software-pipelined: during step k, warp 0
 // updates column k+1 itself and from it forms step k+1's pivot reciprocal
@@ -624,7 +593,7 @@ __device__ void sweep_inverse32(double (&m)[32][33], int* bad) {
   // step 0's pivot and column
   if (warp == 0) {
     double d = m[0][0];
-    if (!pivot_ok(d)) {
+    if (!positive_bits(d)) {
       if (lane == 0) *bad = 1;
       d = 1.0;
     }
@@ -648,7 +617,7 @@ __device__ void sweep_inverse32(double (&m)[32][33], int* bad) {
           v = __fma_rn(-ck[cur][a], cs[cur][bb], m[a][bb]);
         m[a][bb] = v;
         double d = __shfl_sync(0xffffffffu, v, kp);
-        if (!pivot_ok(d)) {
+        if (!positive_bits(d)) {
           if (lane == 0) *bad = 1;
           d = 1.0;
         }
@@ -783,8 +752,9 @@ __global__ void __launch_bounds__(256) k_gj_update(int npad, int P, double* __re
   const int nitems = 4 * nbk * (nbk + 1) / 2;
   const int tid = threadIdx.x, rr = tid >> 5, cc = tid & 31;
   const bool has_next = P + 1 < nbk;
-  double ruo[4], ruh = 0.0;
-  // operands of a bulk quarter (neither index on the pivot block P) into registers
+  double ruo[4], ruh = 0.0, rs = 0.0;
+  // operands of a bulk quarter (neither index on the pivot block P) into
+  // registers, with the entry of S it updates
   auto fetch = [&](int it) {
     if (it >= nitems) return;
     int I, J, q;
@@ -795,7 +765,9 @@ __global__ void __launch_bounds__(256) k_gj_update(int npad, int P, double* __re
       const int e = tid + 256 * u;
       ruo[u] = Uo[(int64_t)(J * 32 + (e >> 5)) * 32 + (e & 31)];
     }
-    ruh = Uh[(int64_t)(I * 32 + q * 8 + rr) * 32 + cc];
+    const int r = I * 32 + q * 8 + rr;
+    ruh = Uh[(int64_t)r * 32 + cc];
+    rs = S[(int64_t)r * npad + J * 32 + cc];
   };
   if (tid == 0) item = atomicAdd(work + P, 1);
   __syncthreads();
@@ -810,6 +782,7 @@ __global__ void __launch_bounds__(256) k_gj_update(int npad, int P, double* __re
     const bool pivq = has_next && I == P + 1 && J == P + 1;
     const bool bulk = I != P && J != P;
     if (!pivq && tid == 0) item = atomicAdd(work + P, 1);
+    const double s_old = rs;
     if (bulk) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -833,7 +806,7 @@ __global__ void __launch_bounds__(256) k_gj_update(int npad, int P, double* __re
       double acc = 0.0;
 #pragma unroll 8
       for (int k = 0; k < 32; ++k) acc += uh[rr][k] * uo[cc][k];
-      *out -= acc;
+      *out = s_old - acc;
     }
     if (pivq) {
       __threadfence();
@@ -1789,6 +1762,14 @@ __global__ void k_pivot_reciprocal(int64_t n, const double* __restrict__ d, doub
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = recip_newton(d[i]);
 }
+__global__ void k_convert(int64_t n, int dir, const void* __restrict__ in, void* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (dir == 0)
+      static_cast<float*>(out)[i] = f32_rn(static_cast<const double*>(in)[i]);
+    else
+      static_cast<double*>(out)[i] = f64_of(static_cast<const float*>(in)[i]);
+  }
+}
 }  // namespace gmg
 
 // The reciprocal the coarsest inverse takes of every pivot, applied to n
@@ -1803,6 +1784,22 @@ extern "C" gmg_status gmg_pivot_reciprocal(int64_t n, const double* d, double* o
   if (n == 0) return GMG_OK;
   const int64_t grid = std::min<int64_t>((n + 255) / 256, 152 * 16);
   k_pivot_reciprocal<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(n, d, out);
+  GMG_LAUNCHED();
+  return GMG_OK;
+}
+
+// The precision conversions of the solver's kernels (done on the bits),
+// applied to n device values (exposed so that they can be checked against
+// the IEEE 754 conversions).
+extern "C" gmg_status gmg_convert(int64_t n, int dir, const void* in, void* out, void* stream) {
+  using namespace gmg;
+  if (n < 0 || (dir != 0 && dir != 1) || (n > 0 && (!in || !out))) {
+    set_error("gmg_convert: negative size, direction not 0 or 1, or null pointer");
+    return GMG_ERR_INVALID_ARG;
+  }
+  if (n == 0) return GMG_OK;
+  const int64_t grid = std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_convert<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(n, dir, in, out);
   GMG_LAUNCHED();
   return GMG_OK;
 }

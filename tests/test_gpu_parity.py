@@ -474,6 +474,63 @@ def test_pivot_reciprocal_within_one_ulp(gmg):
     assert ulps.max() <= 1.0, f"worst {ulps.max()} ulp at d = {d[ulps.argmax()]!r}"
 
 
+def test_bit_conversions_match_ieee(gmg):
+    """The FP64 -> FP32 (round to nearest even) and FP32 -> FP64 conversions
+    that the kernels do on the bit patterns give the IEEE 754 results of the
+    host's conversions, bit for bit: random bit patterns over every exponent,
+    ties and near-ties at each rounding position, the edges of the normal
+    float range (largest float and the overflow to infinity, smallest normal,
+    subnormal results), zeros of both signs, infinities and NaN."""
+    import ctypes
+
+    import torch
+
+    lib = gmg.load_library()
+    rng = np.random.default_rng(11)
+    bits = rng.integers(0, 2**63, 200000, dtype=np.uint64) | (rng.integers(0, 2, 200000, dtype=np.uint64) << np.uint64(63))
+    d = bits.view(np.float64)
+    # values around the float range: exponents 880..1160, mantissas with ties (bit 28 set, lower bits 0) and near-ties
+    ex = rng.integers(880, 1161, 100000).astype(np.uint64)
+    mant = rng.integers(0, 2**52, 100000, dtype=np.uint64)
+    tie = (mant & ~np.uint64(0x1FFFFFFF)) | np.uint64(0x10000000)
+    near = [tie, tie + np.uint64(1), tie - np.uint64(1), mant & ~np.uint64(0x1FFFFFFF)]
+    edge = [((ex << np.uint64(52)) | m).view(np.float64) for m in near]
+    f32max = float(np.finfo(np.float32).max)
+    special = np.array([0.0, -0.0, np.inf, -np.inf, f32max, -f32max, np.nextafter(f32max, np.inf),
+                        f32max * (1 + 2.0**-24), f32max * (1 + 2.0**-25), 2.0**-126, 2.0**-127, 2.0**-149, 2.0**-150,
+                        2.0**-151, 1e-300, 1e300, 1.0, -1.0, 1.0 + 2.0**-24, 1.0 + 3 * 2.0**-24, 5e-324])
+    d = np.concatenate([d, *edge, special, -special])
+    dd = torch.tensor(d, device="cuda")
+    out = torch.empty(d.size, dtype=torch.float32, device="cuda")
+    st = lib.gmg_convert(d.size, 0, ctypes.c_void_p(dd.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == gmg.GMG_OK
+    got = out.cpu().numpy()
+    with np.errstate(over="ignore"):
+        ref = d.astype(np.float32)
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan)
+    bad = np.flatnonzero(got[~nan].view(np.uint32) != ref[~nan].view(np.uint32))
+    assert bad.size == 0, f"{bad.size} narrowing mismatches, first at {d[~nan][bad[0]]!r}"
+    # widening: every float exponent, random mantissas, zeros, subnormals, infinities, NaN
+    fb = rng.integers(0, 2**32, 300000, dtype=np.uint64).astype(np.uint32)
+    f = np.concatenate([fb.view(np.float32), np.array([0.0, -0.0, np.inf, -np.inf, 1e-45, -1e-45, 1.1754942e-38],
+                                                        dtype=np.float32)])
+    ff = torch.tensor(f, device="cuda")
+    out64 = torch.empty(f.size, dtype=torch.float64, device="cuda")
+    st = lib.gmg_convert(f.size, 1, ctypes.c_void_p(ff.data_ptr()), ctypes.c_void_p(out64.data_ptr()),
+                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == gmg.GMG_OK
+    got64 = out64.cpu().numpy()
+    with np.errstate(invalid="ignore"):
+        ref64 = f.astype(np.float64)
+    nan = np.isnan(ref64)
+    assert np.array_equal(np.isnan(got64), nan)
+    assert np.array_equal(got64[~nan].view(np.uint64), ref64[~nan].view(np.uint64))
+    assert lib.gmg_convert(4, 2, ctypes.c_void_p(dd.data_ptr()), ctypes.c_void_p(out.data_ptr()), None) == \
+        gmg.GMG_ERR_INVALID_ARG
+
+
 def _reverse_greedy(A):
     n = A.shape[0]
     col = -np.ones(n, np.int64)
