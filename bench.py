@@ -160,10 +160,16 @@ def gs_level_launch_bytes(dims, l, s):
     return ((z - n) * (s + 4) + 3 * n * s + (C - 1) * n * s) / C
 
 
-def level_breakdown(dims, lanes, levels, cycles, s=4):
+def gs_kernel_name(split, t="float"):
+    return f"k_gs<{t}, {split}>"
+
+
+def level_breakdown(dims, lanes, levels, cycles, s=4, paths=None):
     """Per smoothed level of the timed cycles: Gauss-Seidel launches, average
     launch time and algorithmic GB/s, the transfer (residual, restriction,
-    prolongation) time, and the cluster tail (levels it covers, time)."""
+    prolongation) time, and the cluster tail (levels it covers, time).  A
+    cluster level (paths[l] == 1) runs its sweeps and transfers in two cluster
+    launches: its time per Gauss-Seidel phase includes the transfers."""
     out, tail = [], None
     cyc = max(cycles, 1)
     for l, (gs_ms, gs_n, tr_ms, whole_ms) in enumerate(levels):
@@ -172,7 +178,8 @@ def level_breakdown(dims, lanes, levels, cycles, s=4):
         if gs_n > 0:
             us = 1e3 * gs_ms / gs_n
             b = gs_level_launch_bytes(dims, l, s)
-            out.append({"level": l, "rows": dims[l][0], "colours": dims[l][2], "kernel": f"k_gs<float, {lanes[l]}>",
+            kern = "k_level_cluster" if paths and paths[l] == 1 else gs_kernel_name(lanes[l])
+            out.append({"level": l, "rows": dims[l][0], "colours": dims[l][2], "kernel": kern,
                         "gs_launches_per_cycle": gs_n / cyc, "gs_us_per_launch": us,
                         "gs_bytes_per_launch": b, "gs_gbs": b / (us * 1e-6) / 1e9,
                         "gs_us_per_cycle": 1e3 * gs_ms / cyc, "transfer_us_per_cycle": 1e3 * tr_ms / cyc})
@@ -196,11 +203,13 @@ def dominant_gs(per_level):
     return name, us_cyc / n_cyc, bytes_cyc / n_cyc, us_cyc, lv
 
 
-def ncu_traffic(workload, per_level, levels):
+def ncu_traffic(workload, per_level, levels, kernel):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
     the Gauss-Seidel launches on `levels` of `workload`, from the committed ncu
     capture summary (bytes per launch for each level), weighted by each level's
     launches per V-cycle as the algorithmic bytes are; None if a level is missing."""
+    if not kernel.startswith("k_gs<"):  # the captures are of the one-launch-per-colour kernels
+        return None
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             d = json.load(f)[workload]["gs_bytes_per_launch_by_level"]
@@ -452,7 +461,7 @@ def other_workloads(g, names, steps):
                 pr = sv.profile_read()
                 lv = sv.profile_levels()
                 sv.profile(False)
-                per_level, tail = level_breakdown(sv.dims, lanes, lv, int(pr[3]))
+                per_level, tail = level_breakdown(sv.dims, lanes, lv, int(pr[3]), paths=sv.paths)
                 res[name] = {"rows": s.n, "levels": [d[0] for d in sv.dims], "nnz": [d[1] for d in sv.dims],
                              "colours": [d[2] for d in sv.dims], "fp32_pcg_ms": ms, "iterations": out["r"][1],
                              "vcycle_us_fp32": 1e3 * pr[2] / max(pr[3], 1),
@@ -633,7 +642,7 @@ def main():
     peak, peak_kind = load_peaks()
     smooth_ms, gs_launches, cyc_ms, cycles = pr
     cycles = int(cycles)
-    per_level, tail = level_breakdown(dims, lanes, lv, cycles)
+    per_level, tail = level_breakdown(dims, lanes, lv, cycles, paths=solver.paths)
     kname, k_us, k_bytes, k_us_cyc, k_levels = dominant_gs(per_level)
     achieved = k_bytes / (k_us * 1e-6) / 1e9
     vc_us32 = 1e3 * cyc_ms / max(cycles, 1)
@@ -648,7 +657,7 @@ def main():
     per_level64, _ = level_breakdown(dims, lanes, f_lv, int(f_pr[3]), s=8)
     for r in per_level64:
         r["kernel"] = r["kernel"].replace("float", "double")
-    traffic = ncu_traffic(WORKLOAD, per_level, k_levels)
+    traffic = ncu_traffic(WORKLOAD, per_level, k_levels, kname)
 
     # Sec. 4 hierarchy construction of the same mesh on the GPU, against the host builder
     build_info = None
@@ -698,6 +707,9 @@ def main():
         "config": {
             "workload": WORKLOAD_DESC, "levels": [d[0] for d in dims], "nnz": [d[1] for d in dims],
             "colours": [d[2] for d in dims], "warps_per_row": lanes,
+            "level_paths": solver.paths,
+            "level_paths_legend": "FP32 cycle per level: 0 one launch per colour, 1 cluster level (two cluster "
+                                  "launches), 2 cluster tail, 3 coarsest direct solve",
             "precision": "FP64 conjugate gradients preconditioned by one FP32 V-cycle (nu=2/2, multicolour GS) "
                          "per iteration; FP64 residual, dots and explicit coarsest inverse; the iterations run in a device-side "
                          "graph loop (conditional WHILE node)",

@@ -356,6 +356,16 @@ gmg_status gmg_profile_levels(gmg_handle h, double *out);
 gmg_status gmg_num_levels(gmg_handle h, int *nlev);
 /* rows, stored entries (diagonal included) and colours of level l. */
 gmg_status gmg_level_info(gmg_handle h, int l, int64_t *n, int64_t *nnz, int *ncolors);
+
+/* How the FP32 V-cycle runs level l (the FP64 cycle always uses one launch per
+ * colour): 0 = one kernel launch per Gauss-Seidel colour, residual,
+ * restriction and prolongation; 1 = a cluster level: its sweeps, residual and
+ * restriction in one thread-block-cluster launch and its prolongation and
+ * sweeps in another, rows split over the cluster's CTAs with halo copies in
+ * distributed shared memory (the same arithmetic per row as path 0 with
+ * one warp per row); 2 = inside the cluster tail (this level and all coarser ones in
+ * one launch); 3 = the coarsest level (direct solve).  Errors: INVALID_ARG. */
+gmg_status gmg_level_path(gmg_handle h, int l, int *path);
 /* Copies level l's Galerkin operator A_l (CSR, caller numbering, rowptr n+1,
  * col/val nnz) and its colouring (n) into host buffers; any may be NULL. */
 gmg_status gmg_level_export(gmg_handle h, int l, int64_t *rowptr, int32_t *col, double *val, int32_t *color);

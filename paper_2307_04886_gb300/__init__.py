@@ -29,7 +29,7 @@ EXPORTED = [
     "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_coarse_solve", "gmg_vcycle", "gmg_profile",
     "gmg_profile_read", "gmg_kernel_launches", "gmg_residual_norm_noalloc", "gmg_setup_ML", "gmg_set_t",
     "gmg_mass", "gmg_grad", "gmg_setup_many", "gmg_solve_many", "gmg_destroy_many", "gmg_autotune", "gmg_set_lanes",
-    "gmg_vcycle_batched", "gmg_pivot_reciprocal", "gmg_convert", "gmg_profile_levels", "gmg_grad_pattern",
+    "gmg_vcycle_batched", "gmg_pivot_reciprocal", "gmg_convert", "gmg_level_path", "gmg_profile_levels", "gmg_grad_pattern",
     "gmg_autotune_batched", "gmg_set_lanes_batched", "gmg_autotune_many",
     "gmg_build_hierarchy", "gmg_hierarchy_info", "gmg_hierarchy_level", "gmg_destroy_hierarchy",
 ]
@@ -100,6 +100,7 @@ def load_library(path: str | None = None):
         "gmg_vcycle_batched": (I, [V, I, V, V, V]),
         "gmg_pivot_reciprocal": (I, [I64, V, V, V]),
         "gmg_convert": (I, [I64, I, V, V, V]),
+        "gmg_level_path": (I, [V, I, V]),
         "gmg_profile": (I, [V, I]),
         "gmg_kernel_launches": (ctypes.c_uint64, []),
         "gmg_residual_norm_noalloc": (I, [I64, V, V, V, V, V, V, V, V]),
@@ -219,6 +220,11 @@ class Solver:
             n, nnz, nc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
             lib.gmg_level_info(h, l, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(nc))
             self.dims.append((n.value, nnz.value, nc.value))
+        self.paths = []  # per level, how the FP32 cycle runs it (gmg_level_path)
+        for l in range(self.nlev):
+            p = ctypes.c_int()
+            lib.gmg_level_path(h, l, ctypes.byref(p))
+            self.paths.append(p.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None:

@@ -78,6 +78,13 @@ static gmg_status fetch_scalars(gmg_ctx* c, cudaStream_t s) {
         acc[1] += c->lev_gs[l];
         acc[2] += t0 + t1;
       }
+      if (c->lev_kind[l] == 3) {  // cluster level: its two launches hold the sweeps and the transfers
+        float p0 = 0, p1 = 0;
+        GMG_CK(cudaEventElapsedTime(&p0, E[0], E[1]));
+        GMG_CK(cudaEventElapsedTime(&p1, E[3], E[5]));
+        acc[0] += p0 + p1;
+        acc[1] += c->lev_gs[l];
+      }
       if (c->lev_kind[l] != 0) {
         GMG_CK(cudaEventElapsedTime(&t, E[0], E[5]));
         acc[3] += t;
@@ -420,6 +427,7 @@ gmg_status gmg_solve(gmg_handle h, const double* b, double* x, double tol, int m
     info->rel_res = rel;
   }
   GMG_TRY(inverse_status(c, s));  // the pivot check of an inverse this solve joined
+  GMG_TRY(cluster_level_status(c, s));
   return st;
 }
 
@@ -593,6 +601,19 @@ gmg_status gmg_level_info(gmg_handle h, int l, int64_t* n, int64_t* nnz, int* nc
   if (n) *n = h->L[l].n;
   if (nnz) *nnz = h->L[l].nnz;
   if (ncolors) *ncolors = h->L[l].ncolor;
+  return GMG_OK;
+}
+
+gmg_status gmg_level_path(gmg_handle h, int l, int* path) {
+  if (!h || !path || l < 0 || l >= h->nlev) return GMG_ERR_INVALID_ARG;
+  if (l == h->nlev - 1)
+    *path = 3;
+  else if (h->tail_l0 > 0 && l >= h->tail_l0)
+    *path = 2;
+  else if (h->clev.l > 0 && l == h->clev.l)
+    *path = 1;
+  else
+    *path = 0;
   return GMG_OK;
 }
 

@@ -875,6 +875,22 @@ gmg_status vcycle(gmg_ctx* c, int l, cudaStream_t s, bool c0_done, T* x_in, cons
     return GMG_OK;
   }
   Level& C = c->L[l + 1];
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->clev.l == l && l > 0 && c0_done && !x_in && !b_in) {  // this level on a thread-block cluster
+      if (lp) GMG_CK(record_timing_event(E[0], s));
+      GMG_TRY(launch_cluster_level(c, 0, s));
+      if (lp) GMG_CK(record_timing_event(E[1], s));
+      GMG_TRY(vcycle<T>(c, l + 1, s, true));
+      if (lp) GMG_CK(record_timing_event(E[3], s));
+      GMG_TRY(launch_cluster_level(c, 1, s));
+      if (lp) {
+        GMG_CK(record_timing_event(E[5], s));
+        c->lev_kind[l] = 3;
+        c->lev_gs[l] = c->opt.nu_pre * L.ncolor - 1 + c->opt.nu_post * L.ncolor;
+      }
+      return GMG_OK;
+    }
+  }
   const bool prof = c->prof && l == 0;
   if (prof) GMG_CK(record_timing_event(c->ev[0], s));
   if (lp) GMG_CK(record_timing_event(E[0], s));

@@ -201,7 +201,7 @@ struct Level {
 // its descriptors (passed by value).  Offsets are bytes into the dynamic
 // shared memory of every CTA (the same layout in each).
 constexpr int kMaxTail = 4;            // smoothed levels in the tail
-constexpr int kTailSmemLimit = 200 * 1024;
+constexpr int kTailSmemLimit = 227 * 1024;  // the largest dynamic shared memory of a CTA (no static shared memory)
 struct TailLevel {
   int n, ncolor, nslice, r_nslice;
   int nc0;  // rows of colour 0 (the first rows in the colour-major numbering)
@@ -234,6 +234,54 @@ struct TailDesc {
   TailLevel lv[kMaxTail];
 };
 
+// A smoothed level whose FP32 sweeps, residual, restriction (one launch) and
+// prolongation, sweeps (another) run on one thread-block cluster: the rows
+// are split into ncta contiguous ranges of the caller's numbering (one per
+// CTA, every colour balanced), each CTA keeps x of its rows and of their
+// neighbours owned by other CTAs (the halo) in shared memory, an updated row
+// is stored into the halo copies of the CTAs that read it, and the entries of
+// the next phases' rows stream from L2 into shared memory while the current
+// phase computes.  Per-CTA arrays are concatenated; *_off[cta] is a CTA's
+// start in them.
+constexpr int kClusterStagesMax = 4;  // entry buffers (the current phase and up to three ahead)
+struct ClusterLevel {
+  int l = 0, ncta = 0, threads = 0, ncolor = 0;
+  int nu_pre = 0, nu_post = 0, post_forward = 0, c0_first = 0;
+  int n_loc_max = 0, n_own_max = 0, nsl_max = 0, blk_max = 0;
+  int nstage = 0, push_max = 0;
+  // shared memory: x (own and halo rows), b (own rows), then the set-up image
+  // [o_st, o_st + st_bytes) holding 1/a_ii, a_ii, the slice and colour
+  // tables, the local-to-global rows and the halo stores (copied whole from
+  // img + cta * st_bytes), then the barriers of the copies and the entry stages
+  int o_x = 0, o_b = 0, o_st = 0, st_bytes = 0, o_dinv = 0, o_diag = 0, o_sl = 0, o_csl = 0, o_l2g = 0, o_pp = 0,
+      o_pd = 0, o_mbar = 0, o_buf = 0, smem = 0;
+  const char* img = nullptr;
+  int* err = nullptr;  // set when a bounded wait for an entry block gave up
+  const int32_t *n_own = nullptr, *n_loc = nullptr, *loc_off = nullptr, *loc2glob = nullptr;
+  // slices of each CTA, colour by colour: first local row, rows, width, first
+  // entry (relative to the CTA's entries); csl: first slice of every colour
+  // (+ end), relative to the CTA's slices
+  const int32_t *sl_off = nullptr, *sl_row0 = nullptr, *sl_nrow = nullptr, *sl_w = nullptr, *sl_eoff = nullptr;
+  const int32_t* csl = nullptr;  // ncta x (ncolor + 1)
+  const int64_t* ent_off = nullptr;
+  const float* ent_val = nullptr;  // [k][lane] per slice; refreshed with the level's values
+  const int32_t* ent_col = nullptr;  // local column
+  // halo stores: for each own row, the (CTA << 16 | local index) copies to update
+  const int32_t *push_off = nullptr, *push_ptr = nullptr, *push_dst = nullptr;
+  // the level's global vectors and transfers
+  float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;
+  const float *dinv32 = nullptr, *diag32 = nullptr;
+  const int32_t* p_idx = nullptr;
+  const float* p_w32 = nullptr;
+  const int64_t* r_ptr = nullptr;
+  const int32_t *r_row0 = nullptr, *r_nrow = nullptr, *r_col = nullptr;
+  const float* r_v32 = nullptr;
+  int64_t r_nslice = 0;
+  float *xc32 = nullptr, *bc32 = nullptr;  // next level's x and b
+  const float* dinvc32 = nullptr;
+  int64_t nc0 = 0;  // next level's colour-0 rows (their first update done by the restriction)
+};
+
 }  // namespace gmg
 
 struct gmg_ctx {
@@ -260,6 +308,10 @@ struct gmg_ctx {
   int tail_smem = 0;
   int tail_threads = 1024;
   gmg::TailDesc tail{};
+  // FP32 cycles run level clev.l (0 = none) as two cluster launches
+  gmg::ClusterLevel clev{};
+  int64_t* clev_src = nullptr;  // ELL slot of every cluster-level entry (-1: padding)
+  int64_t clev_nent = 0;
   float* Ainv32 = nullptr;  // coarsest inverse in FP32 for the tail launch
   int* dstatus = nullptr;   // device status words
   // outer iteration (finest level, permuted numbering, FP64)
@@ -320,4 +372,13 @@ gmg_status inverse_status(gmg_ctx* c, cudaStream_t s);
 // Whether a tail cluster of ncta CTAs with `smem` bytes of shared memory each
 // can be scheduled on the device (sets the kernel's attributes).
 gmg_status tail_configure(gmg_ctx* c, int ncta, int threads, int smem, bool* ok);
+// Cluster form of one smoothed level of the FP32 cycle (gmg_clevel.cu): the
+// tables from the level's pattern and numberings (host), the entry values
+// after a numeric set-up, and the two launches (mode 0: pre-smoothing,
+// residual, restriction; mode 1: prolongation, post-smoothing).
+gmg_status build_cluster_level(gmg_ctx* c, int l, const int64_t* rp, const int32_t* ci,
+                               const std::vector<int32_t>& perm, const std::vector<int32_t>& iperm);
+gmg_status refresh_cluster_values(gmg_ctx* c, cudaStream_t s);
+gmg_status launch_cluster_level(gmg_ctx* c, int mode, cudaStream_t s);
+gmg_status cluster_level_status(gmg_ctx* c, cudaStream_t s);
 }  // namespace gmg

@@ -1377,6 +1377,7 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s, bool defer) {
       GMG_LAUNCHED();
     }
   }
+  GMG_TRY(refresh_cluster_values(c, s));
   // coarsest: explicit inverse by block sweeps (on the handle's own stream when deferred)
   const cudaStream_t s_main = s;
   if (defer) {
@@ -1752,6 +1753,10 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   GMG_TRY(a.alloc(&c->dhist, (size_t)c->opt.max_iter + 2));
   GMG_CK(cudaMallocHost((void**)&c->h_scal, 64 * sizeof(double)));
   GMG_TRY(build_tail(c));
+  if (c->tail_l0 >= 2) {
+    const int l = c->tail_l0 - 1;
+    GMG_TRY(build_cluster_level(c, l, hrp[l].data(), hcol[l].data(), perm[l], iperm[l]));
+  }
   return numeric_setup(c, s, false);
 }
 

@@ -531,6 +531,43 @@ def test_bit_conversions_match_ieee(gmg):
         gmg.GMG_ERR_INVALID_ARG
 
 
+def test_cluster_level_matches_colour_launches(gmg, monkeypatch):
+    """The level above the FP32 cycle's cluster tail runs as a cluster level
+    (sweeps, residual, restriction in one cluster launch; prolongation and
+    sweeps in another, halo copies in distributed shared memory).  Its
+    arithmetic per row is that of one warp per row, so with that split the
+    FP32 cycle is bitwise the one-launch-per-colour cycle; it matches the
+    oracle's cycle, and its solves converge to the oracle's solution."""
+    s = gi.torus_system(512, 256, 1e-4, 7)
+    o = oracle.Oracle(s.A, s.Ps)
+    g = gmg.Solver(s.A, s.Ps, precision=gmg.GMG_FP32_PCG)
+    assert g.nlev == 4 and g.paths == [0, 1, 2, 3], g.paths
+    monkeypatch.setenv("GMG_NO_CLUSTER_LEVEL", "1")
+    h = gmg.Solver(s.A, s.Ps, precision=gmg.GMG_FP32_PCG)
+    monkeypatch.delenv("GMG_NO_CLUSTER_LEVEL")
+    assert h.paths == [0, 0, 2, 3], h.paths
+    for sv in (g, h):
+        sv.set_lanes([1] * (sv.nlev - 1))
+    rng = np.random.default_rng(SEED + 21)
+    for x0 in (np.zeros(s.n), rng.standard_normal(s.n)):
+        a = _np(g.vcycle(_t(x0), _t(s.b), fp32=True))
+        b = _np(h.vcycle(_t(x0), _t(s.b), fp32=True))
+        assert np.array_equal(a, b), f"cluster level differs from the colour launches: {np.abs(a - b).max()}"
+        close(a, o.vcycle(x0, s.b), 1e-6, "FP32 cycle with a cluster level", stencil_factor(s.A))
+    x, it, rr, _, st = g.solve(_t(s.b), tol=1e-10)
+    assert st == 0 and np.linalg.norm(s.b - s.A @ _np(x)) <= 1e-10 * np.linalg.norm(s.b)
+    xo, _, _, _ = o.solve(s.b, tol=1e-12, pcg=True)
+    close(_np(x), xo, 1e-8, "solve with a cluster level")
+    # a numeric refresh re-lays the cluster level's entries
+    At = s.A.copy()
+    At.data = At.data * 1.5
+    g.set_values(At.data)
+    h.set_values(At.data)
+    assert np.array_equal(_np(g.vcycle(_t(x0), _t(s.b), fp32=True)), _np(h.vcycle(_t(x0), _t(s.b), fp32=True)))
+    g.close()
+    h.close()
+
+
 def _reverse_greedy(A):
     n = A.shape[0]
     col = -np.ones(n, np.int64)
