@@ -506,12 +506,16 @@ __global__ void k_copy(int64_t n, const double* a, double* b) {
 // the coarsest level run in one launch on one thread-block cluster of ncta
 // CTAs.  Every CTA keeps full copies of x, r, b, 1/a_ii and a_ii of each tail
 // level (and x, b of the coarsest level) in its shared memory, plus the
-// sliced-ELL entries of the slices it owns: slice s of colour range
-// [s0, s1) belongs to CTA (s - s0) mod ncta.  A phase (one Gauss-Seidel
+// sliced-ELL entries of the slices it owns: a slice belongs to the CTA of
+// its first row's range of the caller's numbering (ncta contiguous ranges),
+// so that most neighbours of a row share its CTA.  A phase (one Gauss-Seidel
 // colour, the residual, the restriction, the coarsest GEMV, the
-// prolongation) updates the rows the CTA owns and stores every new value into
-// all CTAs' copies through distributed shared memory; a cluster barrier
-// (release / acquire) ends the phase.  So a phase costs a hardware barrier
+// prolongation) updates the rows the CTA owns and stores every new value
+// through distributed shared memory into the copies that read it: x of a row
+// into the CTAs owning its neighbours or the finer tail level's rows
+// prolongated from it (a per-row mask), the residual, the restricted
+// right-hand side and the coarsest solution into every CTA; a cluster
+// barrier (release / acquire) ends the phase.  So a phase costs a hardware barrier
 // rather than a kernel boundary, and reads global memory only for the
 // restriction and prolongation weights and the coarsest inverse.  Rows of one
 // colour are never adjacent, so a colour phase reads only values that no CTA
@@ -530,6 +534,20 @@ __device__ __forceinline__ unsigned cluster_rank() {
 __device__ __forceinline__ void tail_bcast(float* p, float v, int ncta) {
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
   for (int r = 0; r < ncta; ++r) {
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(r));
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
+  }
+}
+
+// Stores v at p in this CTA and at the same location in every CTA whose bit
+// is set in `mask` (the CTAs that read it).
+__device__ __forceinline__ void tail_push(float* p, float v, unsigned mask) {
+  *p = v;
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  while (mask) {
+    const int r = __ffs(mask) - 1;
+    mask &= mask - 1;
     uint32_t ra;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(r));
     asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
@@ -561,18 +579,21 @@ __device__ __forceinline__ float tail_row_dot(const float* val, const int* col, 
   return acc;
 }
 
-// One Gauss-Seidel colour k over the owned slices of that colour.
-__device__ void tail_colour(const TailLevel& L, char* sm, int k, int cta, int ncta) {
+// One Gauss-Seidel colour k over the owned slices of that colour; each new
+// value goes to this CTA's copy and to the copies of the CTAs that read it.
+__device__ void tail_colour(const TailLevel& L, char* sm, int k) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int* cso = sm_at<int>(sm, L.o_cso);
-  const int s0 = cso[k], s1 = cso[k + 1];
+  const int* own = sm_at<int>(sm, L.o_own);
+  const int* ocs = sm_at<int>(sm, L.o_ocs);
+  const uint16_t* mask = sm_at<uint16_t>(sm, L.o_mask);
   float* x = sm_at<float>(sm, L.o_x);
-  for (int s = s0 + cta + warp * ncta; s < s1; s += nw * ncta) {
+  for (int j = ocs[k] + warp; j < ocs[k + 1]; j += nw) {
+    const int s = own[j];
     const float acc = tail_row_dot(sm_at<float>(sm, L.o_val), sm_at<int>(sm, L.o_col), x,
                                    sm_at<int>(sm, L.o_soff)[s] + lane, sm_at<int>(sm, L.o_width)[s]);
     if (lane < sm_at<int>(sm, L.o_nrow)[s]) {
       const int row = sm_at<int>(sm, L.o_row0)[s] + lane;
-      tail_bcast(x + row, (sm_at<float>(sm, L.o_b)[row] - acc) * sm_at<float>(sm, L.o_dinv)[row], ncta);
+      tail_push(x + row, (sm_at<float>(sm, L.o_b)[row] - acc) * sm_at<float>(sm, L.o_dinv)[row], mask[row]);
     }
   }
 }
@@ -600,7 +621,7 @@ __device__ void tail_owned(const TailLevel& L, char* sm, int mode, const float* 
         const int q = 3 * row;
         const float v = x[row] + (L.p_w32[q] * xn[L.p_idx[q]] + L.p_w32[q + 1] * xn[L.p_idx[q + 1]] +
                                   L.p_w32[q + 2] * xn[L.p_idx[q + 2]]);
-        tail_bcast(x + row, v, ncta);
+        tail_push(x + row, v, sm_at<uint16_t>(sm, L.o_mask)[row]);
       }
     } else if (active) {
       L.x32[row] = x[row];
@@ -628,6 +649,8 @@ __global__ void __launch_bounds__(1024, 1) k_tail_cycle(const __grid_constant__ 
     for (int k = tid; k <= L.ncolor; k += nt) sm_at<int>(sm, L.o_cso)[k] = L.cso[k];
     const int32_t* own = L.own + (int64_t)cta * L.maxown;
     for (int j = tid; j < L.maxown; j += nt) sm_at<int>(sm, L.o_own)[j] = own[j];
+    for (int k = tid; k <= L.ncolor; k += nt) sm_at<int>(sm, L.o_ocs)[k] = L.ocs[(int64_t)cta * (L.ncolor + 1) + k];
+    for (int i = tid; i < L.n; i += nt) sm_at<uint16_t>(sm, L.o_mask)[i] = L.mask[i];
     // owned slices' entries, one warp per slice
     for (int j = warp; j < L.maxown; j += nw) {
       const int s = own[j];
@@ -657,7 +680,7 @@ __global__ void __launch_bounds__(1024, 1) k_tail_cycle(const __grid_constant__ 
     const TailLevel& L = D.lv[t];
     for (int it = 0; it < D.nu_pre; ++it)
       for (int k = (it == 0 && D.c0_first) ? 1 : 0; k < L.ncolor; ++k) {
-        tail_colour(L, sm, k, cta, ncta);
+        tail_colour(L, sm, k);
         tail_sync();
       }
     tail_owned(L, sm, 1, nullptr, ncta);
@@ -707,7 +730,7 @@ __global__ void __launch_bounds__(1024, 1) k_tail_cycle(const __grid_constant__ 
     tail_sync();
     for (int it = 0; it < D.nu_post; ++it)
       for (int q = 0; q < L.ncolor; ++q) {
-        tail_colour(L, sm, D.post_forward ? q : L.ncolor - 1 - q, cta, ncta);
+        tail_colour(L, sm, D.post_forward ? q : L.ncolor - 1 - q);
         tail_sync();
       }
   }

@@ -208,9 +208,11 @@ struct TailLevel {
   // shared-memory copies: x, r, b, 1/a_ii, a_ii (all rows); per slice: first
   // row, rows, width, offset of its entries in the owner's arrays; colour
   // slice offsets; the owned slices' values and columns
-  int o_x, o_r, o_b, o_dinv, o_diag, o_row0, o_nrow, o_width, o_soff, o_cso, o_own, o_val, o_col;
+  int o_x, o_r, o_b, o_dinv, o_diag, o_row0, o_nrow, o_width, o_soff, o_cso, o_own, o_val, o_col, o_ocs, o_mask;
   int maxown;             // owned slices per CTA (list padded with -1)
   const int32_t* own;     // ncta x maxown: each CTA's slices, colour by colour
+  const int32_t* ocs;     // ncta x (ncolor + 1): where each colour starts in a CTA's list
+  const uint16_t* mask;   // per row: the other CTAs that read its x (bit per CTA)
   const int64_t* a_ptr;
   const int32_t *a_row0, *a_nrow, *a_col;
   const float *a_v32, *dinv32, *diag32;

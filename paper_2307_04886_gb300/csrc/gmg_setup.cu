@@ -1545,18 +1545,27 @@ static gmg_status validate(const gmg_csr* A, int nP, const gmg_prolong* P, const
 // their shared-memory copies fit in kTailSmemLimit bytes per CTA; l0 is the
 // smallest level index that fits.  16 CTAs per cluster if the device can
 // schedule them, else 8; off if neither fits or GMG_NO_TAIL=1.
-static gmg_status build_tail(gmg_ctx* c) {
+static gmg_status build_tail(gmg_ctx* c, const std::vector<std::vector<int64_t>>& hrp,
+                             const std::vector<std::vector<int32_t>>& hcol,
+                             const std::vector<std::vector<int32_t>>& perm,
+                             const std::vector<std::vector<int32_t>>& iperm, const gmg_prolong* P) {
   c->tail_l0 = 0;
   const int lam = c->nlev - 1;
   if (const char* e = std::getenv("GMG_NO_TAIL"))
     if (e[0] == '1') return GMG_OK;
   if (lam < 2) return GMG_OK;
   auto al = [](int64_t v) { return (v + 15) & ~(int64_t)15; };
-  // slice widths of every level (host)
+  // slice tables of every candidate level (host)
   std::vector<std::vector<int64_t>> ptr(c->nlev);
+  std::vector<std::vector<int32_t>> row0(c->nlev), nrow(c->nlev);
   for (int l = std::max(1, lam - kMaxTail); l < lam; ++l) {
-    ptr[l].resize(c->L[l].A.nslice + 1);
+    const int64_t ns = c->L[l].A.nslice;
+    ptr[l].resize(ns + 1);
+    row0[l].resize(ns);
+    nrow[l].resize(ns);
     GMG_CK(cudaMemcpy(ptr[l].data(), c->L[l].A.ptr, ptr[l].size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    GMG_CK(cudaMemcpy(row0[l].data(), c->L[l].A.row0, ns * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    GMG_CK(cudaMemcpy(nrow[l].data(), c->L[l].A.nrow, ns * sizeof(int32_t), cudaMemcpyDeviceToHost));
   }
   // cluster size and threads per CTA (GMG_TAIL_CTAS, GMG_TAIL_THREADS override)
   std::vector<int> sizes = {16, 8};
@@ -1568,23 +1577,37 @@ static gmg_status build_tail(gmg_ctx* c) {
     if (ncta < 1 || ncta > 16) continue;
     for (int l0 = std::max(1, lam - kMaxTail); l0 < lam; ++l0) {
       TailDesc D{};
-      std::vector<std::vector<int32_t>> soff(lam), own(lam);
+      std::vector<std::vector<int32_t>> soff(lam), own(lam), ocs(lam), owner(lam);
+      std::vector<std::vector<uint16_t>> mask(lam);
       int64_t cur = 0;
       for (int l = l0; l < lam; ++l) {
         Level& L = c->L[l];
         TailLevel& T = D.lv[l - l0];
-        const int64_t ns = L.A.nslice;
+        const int64_t ns = L.A.nslice, n = L.n;
         soff[l].assign(ns, 0);
+        // a slice belongs to the CTA of its first row's range of the caller's
+        // numbering, so that a row's neighbours mostly share its CTA
+        std::vector<int32_t> slice_cta(ns);
+        owner[l].assign(n, 0);
+        for (int64_t sl = 0; sl < ns; ++sl) {
+          slice_cta[sl] = (int32_t)((int64_t)perm[l][row0[l][sl]] * ncta / n);
+          for (int q = 0; q < nrow[l][sl]; ++q) owner[l][row0[l][sl] + q] = slice_cta[sl];
+        }
         int64_t emax = 0, maxown = 0;
         std::vector<std::vector<int32_t>> ownl(ncta);
+        ocs[l].assign((size_t)ncta * (L.ncolor + 1), 0);
         for (int cta = 0; cta < ncta; ++cta) {
           int64_t off = 0;
-          for (int k = 0; k < L.ncolor; ++k)
-            for (int64_t sl = L.color_slice_off[k] + cta; sl < L.color_slice_off[k + 1]; sl += ncta) {
-              soff[l][sl] = (int32_t)off;
-              off += ptr[l][sl + 1] - ptr[l][sl];
-              ownl[cta].push_back((int32_t)sl);
-            }
+          for (int k = 0; k < L.ncolor; ++k) {
+            ocs[l][(size_t)cta * (L.ncolor + 1) + k] = (int32_t)ownl[cta].size();
+            for (int64_t sl = L.color_slice_off[k]; sl < L.color_slice_off[k + 1]; ++sl)
+              if (slice_cta[sl] == cta) {
+                soff[l][sl] = (int32_t)off;
+                off += ptr[l][sl + 1] - ptr[l][sl];
+                ownl[cta].push_back((int32_t)sl);
+              }
+          }
+          ocs[l][(size_t)cta * (L.ncolor + 1) + L.ncolor] = (int32_t)ownl[cta].size();
           emax = std::max(emax, off);
           maxown = std::max<int64_t>(maxown, (int64_t)ownl[cta].size());
         }
@@ -1592,6 +1615,23 @@ static gmg_status build_tail(gmg_ctx* c) {
         own[l].assign(ncta * maxown, -1);
         for (int cta = 0; cta < ncta; ++cta)
           std::copy(ownl[cta].begin(), ownl[cta].end(), own[l].begin() + cta * maxown);
+        // the CTAs other than its owner that read a row's x: owners of its
+        // neighbours, and (below) owners of the finer tail level's rows that
+        // prolongate from it
+        mask[l].assign(n, 0);
+        for (int64_t r = 0; r < n; ++r) {
+          const int32_t old = perm[l][r];
+          for (int64_t e = hrp[l][old]; e < hrp[l][old + 1]; ++e)
+            mask[l][r] |= (uint16_t)(1u << owner[l][iperm[l][hcol[l][e]]]);
+        }
+        if (l > l0) {
+          const gmg_prolong& Pf = P[l - 1];
+          for (int64_t i = 0; i < Pf.n_fine; ++i)
+            for (int q = 0; q < 3; ++q)
+              if (Pf.w[3 * i + q] != 0.0)
+                mask[l][iperm[l][Pf.idx[3 * i + q]]] |= (uint16_t)(1u << owner[l - 1][iperm[l - 1][i]]);
+        }
+        for (int64_t r = 0; r < n; ++r) mask[l][r] &= (uint16_t)~(1u << owner[l][r]);
         T.maxown = (int)maxown;
         T.n = (int)L.n;
         T.nc0 = (int)L.color_off[1];
@@ -1609,6 +1649,8 @@ static gmg_status build_tail(gmg_ctx* c) {
         T.o_soff = (int)cur; cur = al(cur + 4 * ns);
         T.o_cso = (int)cur; cur = al(cur + 4 * (L.ncolor + 1));
         T.o_own = (int)cur; cur = al(cur + 4 * T.maxown);
+        T.o_ocs = (int)cur; cur = al(cur + 4 * (L.ncolor + 1));
+        T.o_mask = (int)cur; cur = al(cur + 2 * L.n);
         T.o_val = (int)cur; cur = al(cur + 4 * emax);
         T.o_col = (int)cur; cur = al(cur + 4 * emax);
       }
@@ -1627,6 +1669,12 @@ static gmg_status build_tail(gmg_ctx* c) {
         GMG_TRY(upload(c->arena, &so, soff[l].data(), soff[l].size()));
         GMG_TRY(upload(c->arena, &ow, own[l].data(), own[l].size()));
         T.own = ow;
+        int32_t* oc;
+        uint16_t* mk;
+        GMG_TRY(upload(c->arena, &oc, ocs[l].data(), ocs[l].size()));
+        GMG_TRY(upload(c->arena, &mk, mask[l].data(), mask[l].size()));
+        T.ocs = oc;
+        T.mask = mk;
         std::vector<int32_t> cso32(L.color_slice_off.begin(), L.color_slice_off.end());
         GMG_TRY(upload(c->arena, &cs, cso32.data(), cso32.size()));
         T.soff = so;
@@ -1752,7 +1800,7 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   GMG_CK(cudaMemset(c->red_cnt, 0, 4 * sizeof(int)));
   GMG_TRY(a.alloc(&c->dhist, (size_t)c->opt.max_iter + 2));
   GMG_CK(cudaMallocHost((void**)&c->h_scal, 64 * sizeof(double)));
-  GMG_TRY(build_tail(c));
+  GMG_TRY(build_tail(c, hrp, hcol, perm, iperm, P));
   if (c->tail_l0 >= 2) {
     const int l = c->tail_l0 - 1;
     GMG_TRY(build_cluster_level(c, l, hrp[l].data(), hcol[l].data(), perm[l], iperm[l]));
