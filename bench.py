@@ -208,11 +208,15 @@ def ncu_traffic(workload, per_level, levels, kernel):
     the Gauss-Seidel launches on `levels` of `workload`, from the committed ncu
     capture summary (bytes per launch for each level), weighted by each level's
     launches per V-cycle as the algorithmic bytes are; None if a level is missing."""
-    if not kernel.startswith("k_gs<"):  # the captures are of the one-launch-per-colour kernels
-        return None
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
-            d = json.load(f)[workload]["gs_bytes_per_launch_by_level"]
+            j = json.load(f)[workload]
+        if kernel == "k_level_cluster":  # the two launches of a V-cycle, per Gauss-Seidel phase like the bytes
+            r = next(r for r in per_level if r["level"] in levels)
+            return float(j["cluster_level_bytes_per_cycle"]) / r["gs_launches_per_cycle"]
+        if not kernel.startswith("k_gs<"):
+            return None
+        d = j["gs_bytes_per_launch_by_level"]
         num = den = 0.0
         for r in per_level:
             if r["level"] in levels:
