@@ -430,7 +430,6 @@ gmg_status build_cluster_level(gmg_ctx* c, int l, const int64_t* rp, const int32
   std::vector<int32_t> sl_off(ncta + 1, 0), sl_row0, sl_nrow, sl_w, sl_eoff, csl;
   std::vector<int64_t> ent_off(ncta + 1, 0), src;
   std::vector<int32_t> ecol;
-  std::vector<std::vector<int32_t>> halo_local(ncta);  // per CTA: row -> local index, for its halo rows
   int n_loc_max = 0, n_own_max = 0, nsl_max = 0, blk_max = 0;
   for (int t = 0; t < ncta; ++t) {
     // halo: neighbours of own rows owned elsewhere, ascending
