@@ -1353,7 +1353,14 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s, bool defer) {
   GMG_TRY(join_inverse(c, s, false));  // the previous inverse still reads the dense work matrix
   c->inv_check = false;
   GMG_CK(cudaMemsetAsync(c->dstatus, 0, 2 * sizeof(int), s));
-  for (int l = 0; l < c->nlev; ++l) {
+  // level 1's product first: it gathers level 0's CSR values, which the copy
+  // that brought them has just left in L2 (the finest scatter streams far
+  // more than L2 holds and would push them out)
+  std::vector<int> order;
+  if (c->nlev > 1) order.push_back(1);
+  order.push_back(0);
+  for (int l = 2; l < c->nlev; ++l) order.push_back(l);
+  for (int l : order) {
     Level& F = c->L[l];
     if (l > 0) {
       Level& P = c->L[l - 1];
