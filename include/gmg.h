@@ -148,6 +148,19 @@ const char *gmg_last_error(void);
 gmg_status gmg_setup(gmg_handle *h, const gmg_csr *A, int n_prolong, const gmg_prolong *P,
                      const int32_t *const *coloring, const gmg_options *opt, void *stream);
 
+/* The colouring gmg_setup gives a level when the caller passes none (the
+ * multicolour ordering of Sec. 3's Gauss-Seidel relaxation): greedy first
+ * fit in increasing row index and in smallest-last order, each improved by
+ * eight iterated-greedy passes, the one with fewer colours kept (the
+ * index-order one on a tie).  Host only: no GPU is used.  rowptr (n + 1) and
+ * col (rowptr[n]) are a symmetric sparsity pattern with sorted, unique columns
+ * per row (the diagonal may be present); color receives n colours in
+ * [0, *ncolor).  All buffers are the caller's host memory.  Errors:
+ * INVALID_ARG (null pointer, n < 0, rowptr not monotone or not starting at
+ * 0, a column out of range, unsorted or repeated, or a pattern that is not
+ * symmetric). */
+gmg_status gmg_colour(int64_t n, const int64_t *rowptr, const int32_t *col, int32_t *color, int32_t *ncolor);
+
 /* Numeric refresh: new values for A on the SAME sparsity pattern (`val` has
  * rowptr[n] entries in the pattern's order; host or device per `mem`).
  * Recomputes every Galerkin level on the GPU without touching the host-side

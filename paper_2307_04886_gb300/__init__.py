@@ -29,7 +29,7 @@ EXPORTED = [
     "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_coarse_solve", "gmg_vcycle", "gmg_profile",
     "gmg_profile_read", "gmg_kernel_launches", "gmg_residual_norm_noalloc", "gmg_setup_ML", "gmg_set_t",
     "gmg_mass", "gmg_grad", "gmg_setup_many", "gmg_solve_many", "gmg_destroy_many", "gmg_autotune", "gmg_set_lanes",
-    "gmg_vcycle_batched", "gmg_pivot_reciprocal", "gmg_convert", "gmg_level_path", "gmg_profile_levels", "gmg_grad_pattern",
+    "gmg_vcycle_batched", "gmg_pivot_reciprocal", "gmg_convert", "gmg_colour", "gmg_level_path", "gmg_profile_levels", "gmg_grad_pattern",
     "gmg_autotune_batched", "gmg_set_lanes_batched", "gmg_autotune_many",
     "gmg_build_hierarchy", "gmg_hierarchy_info", "gmg_hierarchy_level", "gmg_destroy_hierarchy",
 ]
@@ -100,6 +100,7 @@ def load_library(path: str | None = None):
         "gmg_vcycle_batched": (I, [V, I, V, V, V]),
         "gmg_pivot_reciprocal": (I, [I64, V, V, V]),
         "gmg_convert": (I, [I64, I, V, V, V]),
+        "gmg_colour": (I, [I64, V, V, V, V]),
         "gmg_level_path": (I, [V, I, V]),
         "gmg_profile": (I, [V, I]),
         "gmg_kernel_launches": (ctypes.c_uint64, []),
@@ -140,6 +141,19 @@ def _check(st: int, where: str, ok=(GMG_OK,)):
 
 def _np_ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def colour(A):
+    """The library's colouring of the symmetric sparsity pattern of the scipy
+    CSR matrix `A` (sorted, unique columns): (colour of every row, number of
+    colours).  Host only (`gmg_colour`)."""
+    n = A.shape[0]
+    rp = np.ascontiguousarray(A.indptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.indices, dtype=np.int32)
+    out = np.empty(n, dtype=np.int32)
+    nc = ctypes.c_int32(0)
+    _check(load_library().gmg_colour(n, _np_ptr(rp), _np_ptr(ci), _np_ptr(out), ctypes.byref(nc)), "gmg_colour")
+    return out, int(nc.value)
 
 
 def _stream():

@@ -12,11 +12,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "gmg_internal.cuh"
@@ -880,36 +884,106 @@ static gmg_status upload(Arena& a, T** d, const T* h, size_t n) {
 
 constexpr int kColourPasses = 8;
 
-// First fit in the given visiting order: each row takes the smallest colour
-// not used by a neighbour coloured earlier in this pass.
-static int first_fit(int64_t n, const int64_t* rp, const int32_t* ci, const std::vector<int32_t>& order,
-                     std::vector<int32_t>& color) {
-  color.assign(n, -1);
-  std::vector<int64_t> mark(n + 1, -1);
+// First fit of the rows rows[0 .. cnt) in that order against the colours
+// already in `color` (-1 = not coloured).  `mark` holds one stamp per colour
+// (at least the longest row + 2 entries); `stamp` increases by one per row.
+// The visiting order jumps across the pattern (a class of the previous pass
+// is spread over the whole level), so the pattern entries of the rows a few
+// places ahead are prefetched.
+static int fit_rows(const int32_t* rows, int64_t cnt, const int64_t* rp, const int32_t* ci, int32_t* color,
+                    std::vector<int64_t>& mark, int64_t& stamp) {
+  constexpr int64_t kAhead = 8;
   int ncol = 0;
-  for (int64_t t = 0; t < n; ++t) {
-    const int32_t i = order[t];
+  for (int64_t t = 0; t < cnt; ++t) {
+    if (t + 2 * kAhead < cnt) __builtin_prefetch(&rp[rows[t + 2 * kAhead]]);
+    if (t + kAhead < cnt) {
+      const int64_t k0 = rp[rows[t + kAhead]], k1 = rp[rows[t + kAhead] + 1];
+      for (int64_t k = k0; k < k1; k += 16) __builtin_prefetch(&ci[k]);
+      if (k1 > k0) __builtin_prefetch(&ci[k1 - 1]);
+    }
+    const int32_t i = rows[t];
+    ++stamp;
     for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-      const int32_t j = ci[k];
-      if (j != i && color[j] >= 0) mark[color[j]] = t;
+      const int32_t cj = color[ci[k]];  // the row itself is not coloured yet
+      if (cj >= 0) mark[cj] = stamp;
     }
     int32_t c = 0;
-    while (mark[c] == t) ++c;
+    while (mark[c] == stamp) ++c;
     color[i] = c;
     ncol = std::max(ncol, c + 1);
   }
   return ncol;
 }
 
+// First fit in the given visiting order: each row takes the smallest colour
+// not used by a neighbour coloured earlier in this pass.
+static int first_fit(int64_t n, const int64_t* rp, const int32_t* ci, const std::vector<int32_t>& order,
+                     std::vector<int32_t>& color, int64_t maxlen) {
+  color.assign(n, -1);
+  std::vector<int64_t> mark(maxlen + 2, -1);
+  int64_t stamp = 0;
+  return fit_rows(order.data(), n, rp, ci, color.data(), mark, stamp);
+}
+
+// Barrier of a team of threads that wait by yielding.
+struct YieldBarrier {
+  std::atomic<int> count{0}, gen{0};
+  int n = 1;
+  void wait() {
+    const int g = gen.load(std::memory_order_acquire);
+    if (count.fetch_add(1, std::memory_order_acq_rel) == n - 1) {
+      count.store(0, std::memory_order_relaxed);
+      gen.store(g + 1, std::memory_order_release);
+    } else {
+      while (gen.load(std::memory_order_acquire) == g) std::this_thread::yield();
+    }
+  }
+};
+
 // One iterated-greedy pass: first fit over the classes of `color` from the
-// highest colour down, rows ascending within a class.
-static int iterated_pass(int64_t n, const int64_t* rp, const int32_t* ci, int ncol, std::vector<int32_t>& color) {
+// highest colour down, rows ascending within a class.  The rows of one class
+// are pairwise non-adjacent, so each row's choice depends only on the
+// classes visited before its own: a class is split into contiguous parts
+// coloured by up to `nthreads` threads, with a barrier between classes, and
+// the result is that of the sequential pass.
+static int iterated_pass(int64_t n, const int64_t* rp, const int32_t* ci, int ncol, std::vector<int32_t>& color,
+                         int nthreads, int64_t maxlen) {
   std::vector<int64_t> start(ncol + 1, 0);
   for (int64_t i = 0; i < n; ++i) start[ncol - color[i]]++;  // class of colour c goes to slot ncol - 1 - c
   for (int c = 0; c < ncol; ++c) start[c + 1] += start[c];
+  const std::vector<int64_t> cs(start);  // first position of each class
   std::vector<int32_t> order(n);
   for (int64_t i = 0; i < n; ++i) order[start[ncol - 1 - color[i]]++] = (int32_t)i;
-  return first_fit(n, rp, ci, order, color);
+  color.assign(n, -1);
+  YieldBarrier bar;
+  std::atomic<int> team{0};  // team size once every helper thread is started
+  std::vector<int> nc(std::max(1, nthreads), 0);
+  auto work = [&](int t) {
+    int m;
+    while ((m = team.load(std::memory_order_acquire)) == 0) std::this_thread::yield();
+    if (t >= m) return;
+    std::vector<int64_t> mark(maxlen + 2, -1);
+    int64_t stamp = 0;
+    for (int k = 0; k < ncol; ++k) {
+      const int64_t len = cs[k + 1] - cs[k];
+      const int64_t lo = cs[k] + len * t / m, hi = cs[k] + len * (t + 1) / m;
+      nc[t] = std::max(nc[t], fit_rows(order.data() + lo, hi - lo, rp, ci, color.data(), mark, stamp));
+      if (m > 1) bar.wait();
+    }
+  };
+  std::vector<std::thread> helpers;
+  for (int t = 1; t < nthreads; ++t) {
+    try {
+      helpers.emplace_back(work, t);
+    } catch (...) {  // fewer threads: the team is the ones started
+      break;
+    }
+  }
+  bar.n = 1 + (int)helpers.size();
+  team.store(bar.n, std::memory_order_release);
+  work(0);
+  for (auto& h : helpers) h.join();
+  return *std::max_element(nc.begin(), nc.end());
 }
 
 // Smallest-last order: rows sit in buckets by their number of neighbours not
@@ -960,20 +1034,89 @@ static void smallest_last(int64_t n, const int64_t* rp, const int32_t* ci, std::
   }
 }
 
-static int greedy_colour(int64_t n, const int64_t* rp, const int32_t* ci, std::vector<int32_t>& color) {
-  std::vector<int32_t> order(n), other;
-  for (int64_t i = 0; i < n; ++i) order[i] = (int32_t)i;
-  int na = first_fit(n, rp, ci, order, color);
-  for (int p = 0; p < kColourPasses; ++p) na = iterated_pass(n, rp, ci, na, color);
-  smallest_last(n, rp, ci, order);
-  int nb = first_fit(n, rp, ci, order, other);
-  for (int p = 0; p < kColourPasses; ++p) nb = iterated_pass(n, rp, ci, nb, other);
-  if (nb < na) {
-    color.swap(other);
-    return nb;
+// One candidate: first fit in increasing row index (sl = false) or in
+// smallest-last order (sl = true), then kColourPasses iterated-greedy passes.
+// A pass is a function of the colouring alone, so once the colouring after a
+// pass equals the one two passes earlier the passes alternate between the
+// last two colourings, and the result after all passes is known without
+// running the rest (the same colouring as running them).
+static int colour_candidate(int64_t n, const int64_t* rp, const int32_t* ci, bool sl, std::vector<int32_t>& color) {
+  int64_t maxlen = 0;
+  for (int64_t i = 0; i < n; ++i) maxlen = std::max(maxlen, rp[i + 1] - rp[i]);
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nthreads = n >= (1 << 16) ? (int)std::min(4u, std::max(1u, hw / 4)) : 1;
+  std::vector<int32_t> order(n);
+  if (sl) {
+    smallest_last(n, rp, ci, order);
+  } else {
+    for (int64_t i = 0; i < n; ++i) order[i] = (int32_t)i;
   }
-  return na;
+  int nc = first_fit(n, rp, ci, order, color, maxlen);
+  std::vector<int32_t> prev1, prev2;  // colourings after the previous pass and the one before
+  int nc1 = 0;
+  for (int p = 0; p < kColourPasses; ++p) {
+    prev2.swap(prev1);
+    prev1 = color;
+    nc1 = nc;
+    nc = iterated_pass(n, rp, ci, nc, color, nthreads, maxlen);
+    if (p >= 1 && color == prev2) {
+      if ((kColourPasses - 1 - p) % 2 == 1) {
+        color.swap(prev1);
+        nc = nc1;
+      }
+      break;
+    }
+  }
+  return nc;
 }
+
+// The two candidates of a level, computed on two host threads; the one with
+// fewer colours is kept, the index-order one on a tie.  The threads start as
+// soon as the level's pattern is on the host (while the device computes the
+// next level's pattern) and are joined before the level's layout is built.
+struct ColourJob {
+  int64_t n = 0;
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  std::vector<int32_t> ca, cb;
+  int na = 0, nb = 0;
+  std::thread ta, tb;
+  void start(int64_t n_, const int64_t* rp_, const int32_t* ci_) {
+    n = n_;
+    rp = rp_;
+    ci = ci_;
+    try {
+      ta = std::thread([this] { na = colour_candidate(n, rp, ci, false, ca); });
+      tb = std::thread([this] { nb = colour_candidate(n, rp, ci, true, cb); });
+    } catch (...) {  // no thread available: the candidates are computed in finish()
+    }
+  }
+  // Joins the threads (or computes what they did not) and returns the number
+  // of colours of the kept candidate, moved into `color`.
+  int finish(std::vector<int32_t>& color) {
+    join();
+    if (!started_a) na = colour_candidate(n, rp, ci, false, ca);
+    if (!started_b) nb = colour_candidate(n, rp, ci, true, cb);
+    if (nb < na) {
+      color.swap(cb);
+      return nb;
+    }
+    color.swap(ca);
+    return na;
+  }
+  void join() {
+    if (ta.joinable()) {
+      ta.join();
+      started_a = true;
+    }
+    if (tb.joinable()) {
+      tb.join();
+      started_b = true;
+    }
+  }
+  bool started_a = false, started_b = false;
+  ~ColourJob() { join(); }
+};
 
 // Sliced-ELL structure for `nrows` rows given the rows' entry lists; slices
 // start at every `seg` boundary (colour starts), 32 rows per slice.
@@ -1038,11 +1181,11 @@ static int check_colouring(int l, int64_t n, const int64_t* rp, const int32_t* c
   return nc;
 }
 
-// Colours level l (the caller's colouring when given, else greedy_colour),
+// Colours level l (the caller's colouring when given, else the greedy one of `job`),
 // renumbers it colour by colour (ascending caller index within a colour), and
 // builds the sliced-ELL layout of its off-diagonal part.
 static gmg_status build_level_structure(gmg_ctx* c, int l, const int64_t* rp, const int32_t* ci,
-                                        const int32_t* given, std::vector<int32_t>& perm,
+                                        const int32_t* given, ColourJob& job, std::vector<int32_t>& perm,
                                         std::vector<int32_t>& iperm) {
   Level& L = c->L[l];
   const int64_t n = L.n;
@@ -1052,7 +1195,7 @@ static gmg_status build_level_structure(gmg_ctx* c, int l, const int64_t* rp, co
     if (L.ncolor < 0) return GMG_ERR_INVALID_ARG;
     color.assign(given, given + n);
   } else {
-    L.ncolor = greedy_colour(n, rp, ci, color);
+    L.ncolor = job.finish(color);
   }
   L.h_color = color;
   L.color_off.assign(L.ncolor + 1, 0);
@@ -1073,7 +1216,7 @@ static gmg_status build_level_structure(gmg_ctx* c, int l, const int64_t* rp, co
   EllPlan P;
   plan_slices(L.color_off, rowlen, P, &L.color_slice_off);
   std::vector<int32_t> ecol(P.ptr.back());
-  std::vector<int64_t> c2e(rp[n]);
+  std::vector<int64_t> c2e(l > 0 ? rp[n] : 0);  // level 0 scatters row by row
   for (size_t s = 0; s < P.row0.size(); ++s) {
     const int64_t w = (P.ptr[s + 1] - P.ptr[s]) / kSlice;
     for (int lane = 0; lane < kSlice; ++lane) {
@@ -1083,11 +1226,11 @@ static gmg_status build_level_structure(gmg_ctx* c, int l, const int64_t* rp, co
         const int64_t old = perm[r];
         for (int64_t e = rp[old]; e < rp[old + 1]; ++e) {
           if (ci[e] == old) {
-            c2e[e] = -1 - r;
+            if (l > 0) c2e[e] = -1 - r;
           } else {
             const int64_t slot = P.ptr[s] + k * kSlice + lane;
             ecol[slot] = iperm[ci[e]];
-            c2e[e] = slot;
+            if (l > 0) c2e[e] = slot;
             ++k;
           }
         }
@@ -1201,6 +1344,45 @@ static gmg_status check_err_word(int* d, cudaStream_t s, int* h) {
 }
 
 // Galerkin product of level l into level l+1: symbolic part (pattern).
+// The entries with at least one product term (plan pointer hp), ordered by
+// term count, most terms first, ascending position among equal counts: a
+// stable counting sort.
+static void plan_order(int64_t nnz, const std::vector<int64_t>& hp, std::vector<int32_t>& up) {
+  int64_t wmax = 0;
+  for (int64_t e = 0; e < nnz; ++e) wmax = std::max(wmax, hp[e + 1] - hp[e]);
+  std::vector<int64_t> start(wmax + 2, 0);  // bucket of count w at slot wmax - w
+  for (int64_t e = 0; e < nnz; ++e) {
+    const int64_t w = hp[e + 1] - hp[e];
+    if (w > 0) start[wmax - w + 1]++;
+  }
+  for (int64_t b = 0; b <= wmax; ++b) start[b + 1] += start[b];
+  up.resize(start[wmax + 1]);
+  for (int64_t e = 0; e < nnz; ++e) {
+    const int64_t w = hp[e + 1] - hp[e];
+    if (w > 0) up[start[wmax - w]++] = (int32_t)e;
+  }
+}
+
+// For every entry (J, K) of a pattern with sorted rows, the position of
+// (K, J), -1 for a diagonal entry.  Walking the rows K in increasing order
+// visits the entries (K, J) of each column J in increasing K, i.e. in the
+// order of row J's sorted entries, so a cursor per row pairs them.  Returns
+// false if the pattern is not symmetric.
+static bool mirror_positions(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                             std::vector<int32_t>& m) {
+  m.assign(rp[n], -1);
+  std::vector<int64_t> cur(rp.begin(), rp.end() - 1);
+  for (int64_t K = 0; K < n; ++K)
+    for (int64_t f = rp[K]; f < rp[K + 1]; ++f) {
+      const int64_t J = ci[f];
+      if (J < 0 || J >= n || cur[J] >= rp[J + 1] || ci[cur[J]] != K) return false;
+      m[cur[J]++] = J == K ? -1 : (int32_t)f;
+    }
+  for (int64_t J = 0; J < n; ++J)
+    if (cur[J] != rp[J + 1]) return false;
+  return true;
+}
+
 static gmg_status galerkin_symbolic(gmg_ctx* c, int l, cudaStream_t s, std::vector<int64_t>& hrp,
                                     std::vector<int32_t>& hcol) {
   Level& F = c->L[l];
@@ -1268,9 +1450,7 @@ static gmg_status galerkin_symbolic(gmg_ctx* c, int l, cudaStream_t s, std::vect
   GMG_CK(cudaMemcpyAsync(hp.data(), C.plan_ptr, (C.nnz + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   GMG_CK(cudaStreamSynchronize(s));
   std::vector<int32_t> up;
-  for (int64_t e = 0; e < C.nnz; ++e)
-    if (hp[e + 1] > hp[e]) up.push_back((int32_t)e);
-  std::stable_sort(up.begin(), up.end(), [&](int32_t a, int32_t b) { return hp[a + 1] - hp[a] > hp[b + 1] - hp[b]; });
+  plan_order(C.nnz, hp, up);
   const int64_t nup = (int64_t)up.size();
   if (nup == 0) {
     set_error("Galerkin level " + std::to_string(l + 1) + ": empty product");
@@ -1287,25 +1467,13 @@ static gmg_status galerkin_symbolic(gmg_ctx* c, int l, cudaStream_t s, std::vect
   while ((int64_t)up.size() < 32 * nsl) up.push_back(up.back());  // pad the last slice with a repeated entry
   C.plan_nup = 32 * nsl;
   // CSR position of every entry's mirror (K, J), -1 on the diagonal
-  std::vector<int32_t> row_of(C.nnz);
-  for (int64_t J = 0; J < nc; ++J)
-    for (int64_t e = hrp[J]; e < hrp[J + 1]; ++e) row_of[e] = (int32_t)J;
-  std::vector<int32_t> mir(up.size());
-  for (size_t i = 0; i < up.size(); ++i) {
-    const int32_t J = row_of[up[i]], K = hcol[up[i]];
-    if (K == J) {
-      mir[i] = -1;
-      continue;
-    }
-    const int32_t* b0 = hcol.data() + hrp[K];
-    const int32_t* b1 = hcol.data() + hrp[K + 1];
-    const int32_t* f = std::lower_bound(b0, b1, J);
-    if (f == b1 || *f != J) {
-      set_error("Galerkin level " + std::to_string(l + 1) + ": pattern not symmetric");
-      return GMG_ERR_INVALID_ARG;
-    }
-    mir[i] = (int32_t)(f - hcol.data());
+  std::vector<int32_t> mfull;
+  if (!mirror_positions(nc, hrp, hcol, mfull)) {
+    set_error("Galerkin level " + std::to_string(l + 1) + ": pattern not symmetric");
+    return GMG_ERR_INVALID_ARG;
   }
+  std::vector<int32_t> mir(up.size());
+  for (size_t i = 0; i < up.size(); ++i) mir[i] = mfull[up[i]];
   GMG_TRY(upload(c->arena, &C.plan_mirror, mir.data(), mir.size()));
   GMG_TRY(upload(c->arena, &C.plan_up, up.data(), up.size()));
   GMG_TRY(upload(c->arena, &C.plan_sptr, sptr.data(), sptr.size()));
@@ -1487,19 +1655,26 @@ static gmg_status validate(const gmg_csr* A, int nP, const gmg_prolong* P, const
       return GMG_ERR_NOT_SPD;
     }
   }
-  // symmetry: every (i, j) has a matching (j, i) with the same value
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t k = A->rowptr[i]; k < A->rowptr[i + 1]; ++k) {
-      const int32_t j = A->col[k];
-      if (j <= i) continue;
-      const int32_t* b = A->col + A->rowptr[j];
-      const int32_t* e = A->col + A->rowptr[j + 1];
-      const int32_t* f = std::lower_bound(b, e, (int32_t)i);
-      if (f == e || *f != i || A->val[A->rowptr[j] + (f - b)] != A->val[k]) {
-        set_error("A: not symmetric at (" + std::to_string(i) + ", " + std::to_string(j) + ")");
+  // symmetry: every (i, j) has a matching (j, i) with the same value.  Rows
+  // i in increasing order meet the entries (j, i) of each row j in the order
+  // they are stored (sorted columns), so one cursor per row pairs them.
+  {
+    std::vector<int64_t> cur(A->rowptr, A->rowptr + n);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t k = A->rowptr[i]; k < A->rowptr[i + 1]; ++k) {
+        const int32_t j = A->col[k];
+        const int64_t q = cur[j]++;
+        if (q >= A->rowptr[j + 1] || A->col[q] != i || A->val[q] != A->val[k]) {
+          set_error("A: not symmetric at (" + std::to_string(i) + ", " + std::to_string(j) + ")");
+          return GMG_ERR_NOT_SPD;
+        }
+      }
+    for (int64_t j = 0; j < n; ++j)
+      if (cur[j] != A->rowptr[j + 1]) {
+        set_error("A: not symmetric in row " + std::to_string(j));
         return GMG_ERR_NOT_SPD;
       }
-    }
+  }
   int64_t nf = n;
   for (int l = 0; l < nP; ++l) {
     const gmg_prolong& p = P[l];
@@ -1722,6 +1897,16 @@ static gmg_status build_tail(gmg_ctx* c, const std::vector<std::vector<int64_t>>
 
 gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P, const int32_t* const* coloring,
                       cudaStream_t s) {
+  // wall time of the set-up's parts, printed with GMG_VERBOSE=1
+  using clk = std::chrono::steady_clock;
+  const clk::time_point t_start = clk::now();
+  double t_ms[6] = {0, 0, 0, 0, 0, 0};
+  clk::time_point t_last = t_start;
+  auto lap = [&](int k) {
+    const clk::time_point t = clk::now();
+    t_ms[k] += std::chrono::duration<double, std::milli>(t - t_last).count();
+    t_last = t;
+  };
   GMG_TRY(validate(A, nP, P, coloring));
   GMG_CK(cudaGetDevice(&c->device));
   GMG_CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
@@ -1768,12 +1953,27 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   std::vector<std::vector<int32_t>> hcol(c->nlev);
   hrp[0].assign(A->rowptr, A->rowptr + A->n + 1);
   hcol[0].assign(A->col, A->col + L0.nnz);
-  for (int l = 0; l + 1 < c->nlev; ++l) GMG_TRY(galerkin_symbolic(c, l, s, hrp[l + 1], hcol[l + 1]));
+  // each level's greedy colouring starts on host threads once its pattern is
+  // here, overlapping the device's symbolic pass of the next level
+  std::vector<std::unique_ptr<ColourJob>> jobs(c->nlev);
+  for (auto& j : jobs) j.reset(new ColourJob);
+  auto start_colouring = [&](int l) {
+    if (!(coloring && coloring[l])) jobs[l]->start(c->L[l].n, hrp[l].data(), hcol[l].data());
+  };
+  lap(0);
+  start_colouring(0);
+  for (int l = 0; l + 1 < c->nlev; ++l) {
+    GMG_TRY(galerkin_symbolic(c, l, s, hrp[l + 1], hcol[l + 1]));
+    start_colouring(l + 1);
+  }
+  lap(1);
+  for (auto& j : jobs) j->join();
+  lap(2);
   // colouring, renumbering, layouts
   std::vector<std::vector<int32_t>> perm(c->nlev), iperm(c->nlev);
   for (int l = 0; l < c->nlev; ++l)
-    GMG_TRY(build_level_structure(c, l, hrp[l].data(), hcol[l].data(), coloring ? coloring[l] : nullptr, perm[l],
-                                  iperm[l]));
+    GMG_TRY(build_level_structure(c, l, hrp[l].data(), hcol[l].data(), coloring ? coloring[l] : nullptr, *jobs[l],
+                                  perm[l], iperm[l]));
   for (int l = 0; l + 1 < c->nlev; ++l)
     GMG_TRY(build_transfer_structure(c, l, P[l], perm[l], iperm[l], perm[l + 1], iperm[l + 1]));
   // coarsest dense buffers
@@ -1807,12 +2007,25 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   GMG_CK(cudaMemset(c->red_cnt, 0, 4 * sizeof(int)));
   GMG_TRY(a.alloc(&c->dhist, (size_t)c->opt.max_iter + 2));
   GMG_CK(cudaMallocHost((void**)&c->h_scal, 64 * sizeof(double)));
+  lap(3);
   GMG_TRY(build_tail(c, hrp, hcol, perm, iperm, P));
   if (c->tail_l0 >= 2) {
     const int l = c->tail_l0 - 1;
     GMG_TRY(build_cluster_level(c, l, hrp[l].data(), hcol[l].data(), perm[l], iperm[l]));
   }
-  return numeric_setup(c, s, false);
+  lap(4);
+  const gmg_status st = numeric_setup(c, s, false);
+  if (const char* e = std::getenv("GMG_VERBOSE"))
+    if (e[0] == '1' && st == GMG_OK) {
+      cudaStreamSynchronize(s);
+      lap(5);
+      std::fprintf(stderr,
+                   "gmg: set-up %.1f ms: validation and uploads %.1f, symbolic Galerkin %.1f, colouring wait %.1f, "
+                   "layouts and transfers %.1f, tail and cluster level %.1f, numeric set-up %.1f\n",
+                   std::chrono::duration<double, std::milli>(t_last - t_start).count(), t_ms[0], t_ms[1], t_ms[2],
+                   t_ms[3], t_ms[4], t_ms[5]);
+    }
+  return st;
 }
 
 }  // namespace gmg
@@ -1831,6 +2044,48 @@ __global__ void k_convert(int64_t n, int dir, const void* __restrict__ in, void*
   }
 }
 }  // namespace gmg
+
+// The library's colouring of a symmetric pattern, on the host.
+extern "C" gmg_status gmg_colour(int64_t n, const int64_t* rowptr, const int32_t* col, int32_t* color,
+                                 int32_t* ncolor) {
+  using namespace gmg;
+  if (n < 0 || !rowptr || !ncolor || (n > 0 && (!col || !color))) {
+    set_error("gmg_colour: negative size or null pointer");
+    return GMG_ERR_INVALID_ARG;
+  }
+  if (n > INT32_MAX || rowptr[0] != 0) {
+    set_error("gmg_colour: n exceeds the 32-bit index range or rowptr[0] != 0");
+    return GMG_ERR_INVALID_ARG;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (rowptr[i + 1] < rowptr[i]) {
+      set_error("gmg_colour: rowptr not monotone");
+      return GMG_ERR_INVALID_ARG;
+    }
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+      if (col[k] < 0 || col[k] >= n || (k > rowptr[i] && col[k] <= col[k - 1])) {
+        set_error("gmg_colour: column out of range, unsorted or repeated in row " + std::to_string(i));
+        return GMG_ERR_INVALID_ARG;
+      }
+  }
+  const std::vector<int64_t> rp(rowptr, rowptr + n + 1);
+  const std::vector<int32_t> ci(col, col + rowptr[n]);
+  std::vector<int32_t> mirror;
+  if (!mirror_positions(n, rp, ci, mirror)) {
+    set_error("gmg_colour: pattern not symmetric");
+    return GMG_ERR_INVALID_ARG;
+  }
+  if (n == 0) {
+    *ncolor = 0;
+    return GMG_OK;
+  }
+  ColourJob job;
+  job.start(n, rp.data(), ci.data());
+  std::vector<int32_t> c;
+  *ncolor = job.finish(c);
+  std::copy(c.begin(), c.end(), color);
+  return GMG_OK;
+}
 
 // The reciprocal the coarsest inverse takes of every pivot, applied to n
 // device values (exposed so that its accuracy can be checked against the

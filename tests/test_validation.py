@@ -95,6 +95,15 @@ def test_asymmetric(g):
     assert st == g.GMG_ERR_NOT_SPD and "not symmetric" in msg
 
 
+def test_asymmetric_pattern(g):
+    # an entry without its mirror, early and late in the row order
+    for i, j in ((1, 6), (6, 1), (0, 7)):
+        A = _lap1d(8).tolil()
+        A[i, j] = -0.1
+        st, msg = _setup(g, A.tocsr())
+        assert st == g.GMG_ERR_NOT_SPD and "not symmetric" in msg, (i, j, msg)
+
+
 def test_non_finite_values(g):
     A = _lap1d(8).tolil()
     A[4, 4] = np.nan
