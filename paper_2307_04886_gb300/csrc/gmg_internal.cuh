@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdint>
 #include <cstdlib>
 #include <string>
@@ -96,11 +97,16 @@ inline gmg_status launch(void (*k)(P...), int64_t grid, int block, cudaStream_t 
 // Device allocation registry of a handle: everything is freed by gmg_destroy.
 struct Arena {
   std::vector<void*> ptrs;
+  double ms_alloc = 0.0, ms_copy = 0.0;  // host time in cudaMalloc and in uploads (GMG_VERBOSE=1 reports it)
+  int64_t n_alloc = 0;
   template <class T>
   gmg_status alloc(T** p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
+    const auto t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    ms_alloc += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    ++n_alloc;
     if (e != cudaSuccess) {
       set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
       return GMG_ERR_OOM;

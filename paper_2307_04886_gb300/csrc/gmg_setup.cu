@@ -869,7 +869,9 @@ static int grid_for(int64_t work, int threads, int cap = 152 * 32) {
 template <class T>
 static gmg_status upload(Arena& a, T** d, const T* h, size_t n) {
   GMG_TRY(a.alloc(d, n));
+  const auto t0 = std::chrono::steady_clock::now();
   if (n) GMG_CK(cudaMemcpy(*d, h, n * sizeof(T), cudaMemcpyHostToDevice));
+  a.ms_copy += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return GMG_OK;
 }
 
@@ -1900,7 +1902,7 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   // wall time of the set-up's parts, printed with GMG_VERBOSE=1
   using clk = std::chrono::steady_clock;
   const clk::time_point t_start = clk::now();
-  double t_ms[6] = {0, 0, 0, 0, 0, 0};
+  double t_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   clk::time_point t_last = t_start;
   auto lap = [&](int k) {
     const clk::time_point t = clk::now();
@@ -1974,8 +1976,10 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   for (int l = 0; l < c->nlev; ++l)
     GMG_TRY(build_level_structure(c, l, hrp[l].data(), hcol[l].data(), coloring ? coloring[l] : nullptr, *jobs[l],
                                   perm[l], iperm[l]));
+  lap(6);
   for (int l = 0; l + 1 < c->nlev; ++l)
     GMG_TRY(build_transfer_structure(c, l, P[l], perm[l], iperm[l], perm[l + 1], iperm[l + 1]));
+  lap(7);
   // coarsest dense buffers
   c->nco = c->L[c->nlev - 1].n;
   {
@@ -2021,9 +2025,11 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
       lap(5);
       std::fprintf(stderr,
                    "gmg: set-up %.1f ms: validation and uploads %.1f, symbolic Galerkin %.1f, colouring wait %.1f, "
-                   "layouts and transfers %.1f, tail and cluster level %.1f, numeric set-up %.1f\n",
+                   "level layouts %.1f, transfer layouts %.1f, vectors %.1f, tail and cluster level %.1f, "
+                   "numeric set-up %.1f; in all: %lld cudaMalloc %.1f, uploads %.1f\n",
                    std::chrono::duration<double, std::milli>(t_last - t_start).count(), t_ms[0], t_ms[1], t_ms[2],
-                   t_ms[3], t_ms[4], t_ms[5]);
+                   t_ms[6], t_ms[7], t_ms[3], t_ms[4], t_ms[5], (long long)c->arena.n_alloc, c->arena.ms_alloc,
+                   c->arena.ms_copy);
     }
   return st;
 }
