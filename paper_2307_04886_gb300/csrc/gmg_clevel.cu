@@ -410,9 +410,10 @@ gmg_status build_cluster_level(gmg_ctx* c, int l, const int64_t* rp, const int32
   std::vector<int32_t> colour(n);
   for (int k = 0; k < L.ncolor; ++k)
     for (int64_t r = L.color_off[k]; r < L.color_off[k + 1]; ++r) colour[r] = k;
-  // owner of every row: contiguous ranges of the caller's numbering
+  // owner of every row: contiguous ranges of the locality rank (the caller's
+  // numbering where that is local)
   std::vector<int32_t> owner(n);
-  for (int64_t r = 0; r < n; ++r) owner[r] = (int32_t)((int64_t)perm[r] * ncta / n);
+  for (int64_t r = 0; r < n; ++r) owner[r] = (int32_t)((int64_t)L.h_key[perm[r]] * ncta / n);
   // off-diagonal neighbours of a row in ELL entry order
   auto neighbours = [&](int64_t r, std::vector<int32_t>& out) {
     out.clear();

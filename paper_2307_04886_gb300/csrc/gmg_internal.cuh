@@ -153,6 +153,7 @@ struct Level {
   std::vector<int64_t> color_off;        // host: first permuted row of each colour (+ end)
   std::vector<int64_t> color_slice_off;  // host: first slice of each colour (+ end)
   std::vector<int32_t> h_color;          // host: colour of every row (caller numbering)
+  std::vector<int32_t> h_key;            // host: locality rank of every row (caller numbering)
   // numbering: perm[new] = old, iperm[old] = new
   int32_t* perm = nullptr;
   int32_t* iperm = nullptr;

@@ -1183,8 +1183,55 @@ static int check_colouring(int l, int64_t n, const int64_t* rp, const int32_t* c
   return nc;
 }
 
+// Locality rank of every row of every level (a permutation of 0 .. n_l - 1):
+// the order of rows within a colour, and the ranges that the cluster kernels
+// give their CTAs.  Rows of one colour are independent, so this order changes
+// no result of a Gauss-Seidel sweep; it decides which values a warp's gathers
+// touch together.  It is the caller's index where the caller's numbering is
+// local (at most a tenth of the off-diagonal entries join rows more than 4,096
+// indices apart, e.g. a structured mesh), else the order of the hierarchy's
+// tree: rows sorted by the rank of their heaviest coarse parent (the first of
+// equal weights), then by caller index, so that the rows under one coarse
+// row, and under one coarser ancestor, are consecutive (a point cloud in
+// random order).  The coarsest level keeps the caller's order.
+static void locality_ranks(gmg_ctx* c, const std::vector<std::vector<int64_t>>& hrp,
+                           const std::vector<std::vector<int32_t>>& hcol, const gmg_prolong* P) {
+  const int nlev = c->nlev;
+  for (int l = nlev - 1; l >= 0; --l) {
+    Level& L = c->L[l];
+    const int64_t n = L.n;
+    L.h_key.resize(n);
+    int64_t off = 0, far = 0;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t k = hrp[l][i]; k < hrp[l][i + 1]; ++k) {
+        const int64_t d = (int64_t)hcol[l][k] - i;
+        off += d != 0;
+        far += d > 4096 || d < -4096;
+      }
+    const char* e = std::getenv("GMG_CALLER_ORDER");
+    if (l == nlev - 1 || 10 * far <= off || (e && e[0] == '1')) {
+      for (int64_t i = 0; i < n; ++i) L.h_key[i] = (int32_t)i;
+      continue;
+    }
+    const gmg_prolong& p = P[l];
+    const std::vector<int32_t>& kc = c->L[l + 1].h_key;
+    std::vector<int32_t> pk(n);
+    for (int64_t i = 0; i < n; ++i) {
+      int q = 0;
+      for (int s = 1; s < 3; ++s)
+        if (p.w[3 * i + s] > p.w[3 * i + q]) q = s;
+      pk[i] = kc[p.idx[3 * i + q]];
+    }
+    // stable counting sort by parent rank
+    std::vector<int64_t> start(p.n_coarse + 1, 0);
+    for (int64_t i = 0; i < n; ++i) start[pk[i] + 1]++;
+    for (int64_t J = 0; J < p.n_coarse; ++J) start[J + 1] += start[J];
+    for (int64_t i = 0; i < n; ++i) L.h_key[i] = (int32_t)start[pk[i]]++;
+  }
+}
+
 // Colours level l (the caller's colouring when given, else the greedy one of `job`),
-// renumbers it colour by colour (ascending caller index within a colour), and
+// renumbers it colour by colour (ascending locality rank within a colour), and
 // builds the sliced-ELL layout of its off-diagonal part.
 static gmg_status build_level_structure(gmg_ctx* c, int l, const int64_t* rp, const int32_t* ci,
                                         const int32_t* given, ColourJob& job, std::vector<int32_t>& perm,
@@ -1206,10 +1253,13 @@ static gmg_status build_level_structure(gmg_ctx* c, int l, const int64_t* rp, co
   perm.assign(n, 0);
   iperm.assign(n, 0);
   {
+    std::vector<int32_t> byrank(n);
+    for (int64_t i = 0; i < n; ++i) byrank[L.h_key[i]] = (int32_t)i;
     std::vector<int64_t> fill(L.color_off.begin(), L.color_off.end() - 1);
-    for (int64_t i = 0; i < n; ++i) {
+    for (int64_t t = 0; t < n; ++t) {
+      const int32_t i = byrank[t];
       const int64_t r = fill[color[i]]++;
-      perm[r] = (int32_t)i;
+      perm[r] = i;
       iperm[i] = (int32_t)r;
     }
   }
@@ -1774,7 +1824,7 @@ static gmg_status build_tail(gmg_ctx* c, const std::vector<std::vector<int64_t>>
         std::vector<int32_t> slice_cta(ns);
         owner[l].assign(n, 0);
         for (int64_t sl = 0; sl < ns; ++sl) {
-          slice_cta[sl] = (int32_t)((int64_t)perm[l][row0[l][sl]] * ncta / n);
+          slice_cta[sl] = (int32_t)((int64_t)c->L[l].h_key[perm[l][row0[l][sl]]] * ncta / n);
           for (int q = 0; q < nrow[l][sl]; ++q) owner[l][row0[l][sl] + q] = slice_cta[sl];
         }
         int64_t emax = 0, maxown = 0;
@@ -1968,6 +2018,7 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
     GMG_TRY(galerkin_symbolic(c, l, s, hrp[l + 1], hcol[l + 1]));
     start_colouring(l + 1);
   }
+  locality_ranks(c, hrp, hcol, P);
   lap(1);
   for (auto& j : jobs) j->join();
   lap(2);
