@@ -1187,30 +1187,56 @@ static int check_colouring(int l, int64_t n, const int64_t* rp, const int32_t* c
 // the order of rows within a colour, and the ranges that the cluster kernels
 // give their CTAs.  Rows of one colour are independent, so this order changes
 // no result of a Gauss-Seidel sweep; it decides which values a warp's gathers
-// touch together.  It is the caller's index where the caller's numbering is
-// local (at most a tenth of the off-diagonal entries join rows more than 4,096
-// indices apart, e.g. a structured mesh), else the order of the hierarchy's
-// tree: rows sorted by the rank of their heaviest coarse parent (the first of
-// equal weights), then by caller index, so that the rows under one coarse
-// row, and under one coarser ancestor, are consecutive (a point cloud in
-// random order).  The coarsest level keeps the caller's order.
+// touch together and which rows share a CTA.  It is the caller's index where
+// the caller's numbering is local (at most a fifth of the off-diagonal
+// entries join rows more than max(32, n/32) indices apart, e.g. a structured
+// mesh).  Otherwise the coarsest level takes breadth-first order (from the
+// smallest unvisited row, neighbours in pattern order) and the finer levels
+// the order of the hierarchy's tree: rows sorted by the rank of their
+// heaviest coarse parent (the first of equal weights), then by caller index,
+// so that the rows under one coarse row, and under one coarser ancestor, are
+// consecutive (a point cloud in random order).
 static void locality_ranks(gmg_ctx* c, const std::vector<std::vector<int64_t>>& hrp,
                            const std::vector<std::vector<int32_t>>& hcol, const gmg_prolong* P) {
   const int nlev = c->nlev;
+  const char* env = std::getenv("GMG_CALLER_ORDER");
+  const bool caller_only = env && env[0] == '1';
   for (int l = nlev - 1; l >= 0; --l) {
     Level& L = c->L[l];
     const int64_t n = L.n;
+    const int64_t* rp = hrp[l].data();
+    const int32_t* ci = hcol[l].data();
     L.h_key.resize(n);
+    const int64_t span = std::max<int64_t>(32, n / 32);
     int64_t off = 0, far = 0;
     for (int64_t i = 0; i < n; ++i)
-      for (int64_t k = hrp[l][i]; k < hrp[l][i + 1]; ++k) {
-        const int64_t d = (int64_t)hcol[l][k] - i;
+      for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+        const int64_t d = (int64_t)ci[k] - i;
         off += d != 0;
-        far += d > 4096 || d < -4096;
+        far += d > span || d < -span;
       }
-    const char* e = std::getenv("GMG_CALLER_ORDER");
-    if (l == nlev - 1 || 10 * far <= off || (e && e[0] == '1')) {
+    if (caller_only || 5 * far <= off) {
       for (int64_t i = 0; i < n; ++i) L.h_key[i] = (int32_t)i;
+      continue;
+    }
+    if (l == nlev - 1) {
+      std::vector<int32_t> queue(n);
+      std::vector<char> seen(n, 0);
+      int64_t head = 0, tail = 0;
+      for (int64_t s0 = 0; s0 < n; ++s0) {
+        if (seen[s0]) continue;
+        seen[s0] = 1;
+        queue[tail++] = (int32_t)s0;
+        while (head < tail) {
+          const int32_t u = queue[head];
+          L.h_key[u] = (int32_t)head++;
+          for (int64_t k = rp[u]; k < rp[u + 1]; ++k)
+            if (!seen[ci[k]]) {
+              seen[ci[k]] = 1;
+              queue[tail++] = ci[k];
+            }
+        }
+      }
       continue;
     }
     const gmg_prolong& p = P[l];
