@@ -479,6 +479,33 @@ def other_workloads(g, names, steps):
     return res
 
 
+def profile_config(args):
+    """One workload's solves for a kernel profiler: the launch sequence of the
+    timed solve, with a fixed warps-per-row split instead of the autotuner."""
+    import torch
+
+    import gmg_inputs as gi
+    import paper_2307_04886_gb300 as g
+
+    g.build_library()
+    torch.cuda.set_device(0)
+    s = gi.workload(args.profile_config)
+    sv = g.Solver(s.A, s.Ps, precision=g.GMG_FP32_PCG)
+    if args.lanes:
+        ln = [int(v) for v in args.lanes.split(",")]
+        sv.set_lanes((ln + [ln[-1]] * len(sv.dims))[:max(1, len(sv.dims) - 1)])
+    b = torch.tensor(s.b, device="cuda")
+    x = torch.zeros_like(b)
+    for _ in range(args.warmup + 1):
+        x.zero_()
+        r = sv.solve(b, x, tol=1e-10)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_config": args.profile_config, "levels": [d[0] for d in sv.dims],
+                      "iterations": r[1], "level_paths": sv.paths}), flush=True)
+    sv.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -493,11 +520,16 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="set up, autotune, run `warmup` untimed steps and one step, print a short note and exit "
                          "(the launch sequence a kernel profiler lists; no timing is reported)")
+    ap.add_argument("--profile-config", default=None,
+                    help="set up the named other workload (e.g. cloud4m) with the --lanes split, run `warmup` + 1 "
+                         "solves to 1e-10, print a short note and exit (for kernel profilers; no timing)")
     ap.add_argument("--lanes", default=None,
                     help="comma-separated warps-per-row split of every smoothed level (instead of the autotuner)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_config:
+        return profile_config(args)
 
     ws, rank, local = dist_env()
     # inputs of the other workloads that take long to generate, prepared by a

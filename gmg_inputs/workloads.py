@@ -243,6 +243,8 @@ def workload(name: str) -> System:
         return cached(name, heat_system)
     if name == "cloud4m":
         return cached(name, cloud_system, 4194304)
+    if name == "cloud1m":  # the same recipe at 1,048,576 points (kernel captures that must stay small)
+        return cached(name, cloud_system, 1048576)
     if name == "book5":
         return cached(name, nonmanifold_system)
     raise KeyError(name)
