@@ -366,6 +366,15 @@ gmg_status gmg_profile_read(gmg_handle h, double *out /* 4 */);
 gmg_status gmg_profile_levels(gmg_handle h, double *out);
 
 /* ---- introspection (host outputs) ---- */
+/* Warnings of the set-up (conditions that are not errors: the solve runs as
+ * usual).  GMG_WARN_P_UNITY: the weights of some row of some P_l do not sum
+ * to 1 within 1e-12 (the barycentric weights of Sec. 4.4, and the fallback's
+ * normalised weights, sum to 1, so that a constant on a coarse level
+ * prolongs to a constant).  *flags receives the OR of the warning bits;
+ * max_dev, if not NULL, receives the largest |sum_k w_ik - 1| over the rows
+ * of every P_l.  Errors: INVALID_ARG (null handle or flags). */
+#define GMG_WARN_P_UNITY 1u
+gmg_status gmg_warnings(gmg_handle h, uint32_t *flags, double *max_dev);
 gmg_status gmg_num_levels(gmg_handle h, int *nlev);
 /* rows, stored entries (diagonal included) and colours of level l. */
 gmg_status gmg_level_info(gmg_handle h, int l, int64_t *n, int64_t *nnz, int *ncolors);

@@ -22,10 +22,11 @@ GMG_OK, GMG_ERR_INVALID_ARG, GMG_ERR_NOT_SPD, GMG_ERR_EMPTY_P_COLUMN, GMG_ERR_CH
     GMG_ERR_NONFINITE, GMG_ERR_OOM, GMG_ERR_CUDA, GMG_ERR_TIMEOUT, GMG_ERR_TOO_LARGE = range(11)
 GMG_FP64, GMG_FP32_REFINE, GMG_FP32_PCG, GMG_FP64_PCG = 0, 1, 2, 3
 GMG_MEM_DEVICE, GMG_MEM_HOST = 0, 1
+GMG_WARN_P_UNITY = 1
 
 EXPORTED = [
     "gmg_default_options", "gmg_status_string", "gmg_last_error", "gmg_setup", "gmg_set_values", "gmg_solve",
-    "gmg_solve_batched", "gmg_destroy", "gmg_num_levels", "gmg_level_info", "gmg_level_export", "gmg_smooth",
+    "gmg_solve_batched", "gmg_destroy", "gmg_warnings", "gmg_num_levels", "gmg_level_info", "gmg_level_export", "gmg_smooth",
     "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_coarse_solve", "gmg_vcycle", "gmg_profile",
     "gmg_profile_read", "gmg_kernel_launches", "gmg_residual_norm_noalloc", "gmg_setup_ML", "gmg_set_t",
     "gmg_mass", "gmg_grad", "gmg_setup_many", "gmg_solve_many", "gmg_destroy_many", "gmg_autotune", "gmg_set_lanes",
@@ -88,6 +89,7 @@ def load_library(path: str | None = None):
         "gmg_solve": (I, [V, V, V, D, I, V, V]),
         "gmg_solve_batched": (I, [V, I, V, V, D, I, V, V]),
         "gmg_destroy": (I, [V]),
+        "gmg_warnings": (I, [V, V, V]),
         "gmg_num_levels": (I, [V, V]),
         "gmg_level_info": (I, [V, I, V, V, V]),
         "gmg_level_export": (I, [V, I, V, V, V, V]),
@@ -239,6 +241,10 @@ class Solver:
             p = ctypes.c_int()
             lib.gmg_level_path(h, l, ctypes.byref(p))
             self.paths.append(p.value)
+        fl, dev = ctypes.c_uint32(0), ctypes.c_double(0.0)
+        _check(lib.gmg_warnings(h, ctypes.byref(fl), ctypes.byref(dev)), "gmg_warnings")
+        self.warnings = fl.value  # GMG_WARN_P_UNITY: some P_l row's weights do not sum to 1 within 1e-12
+        self.p_unity_dev = dev.value  # largest |sum_k w_ik - 1| over every P_l
 
     def close(self):
         if getattr(self, "_h", None) is not None:

@@ -596,6 +596,13 @@ gmg_status gmg_num_levels(gmg_handle h, int* nlev) {
   return GMG_OK;
 }
 
+gmg_status gmg_warnings(gmg_handle h, uint32_t* flags, double* max_dev) {
+  if (!h || !flags) return GMG_ERR_INVALID_ARG;
+  *flags = h->p_unity_dev > 1e-12 ? GMG_WARN_P_UNITY : 0u;
+  if (max_dev) *max_dev = h->p_unity_dev;
+  return GMG_OK;
+}
+
 gmg_status gmg_level_info(gmg_handle h, int l, int64_t* n, int64_t* nnz, int* ncolors) {
   if (!h || l < 0 || l >= h->nlev) return GMG_ERR_INVALID_ARG;
   if (n) *n = h->L[l].n;

@@ -297,6 +297,7 @@ struct gmg_ctx {
   gmg_options opt{};
   int device = 0;
   int nlev = 0;
+  double p_unity_dev = 0.0;  // largest |sum_k w_ik - 1| over the rows of every P_l
   std::vector<gmg::Level> L;
   gmg::Arena arena;
   // coarsest level

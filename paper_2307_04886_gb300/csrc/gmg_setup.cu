@@ -1690,7 +1690,8 @@ gmg_status numeric_setup(gmg_ctx* c, cudaStream_t s, bool defer) {
 }
 
 // ---- validation (host) ----
-static gmg_status validate(const gmg_csr* A, int nP, const gmg_prolong* P, const int32_t* const* coloring) {
+static gmg_status validate(const gmg_csr* A, int nP, const gmg_prolong* P, const int32_t* const* coloring,
+                           double* unity_dev) {
   if (!A || A->n <= 0 || !A->rowptr || !A->col || !A->val) {
     set_error("A: null pointer or n <= 0");
     return GMG_ERR_INVALID_ARG;
@@ -1761,7 +1762,9 @@ static gmg_status validate(const gmg_csr* A, int nP, const gmg_prolong* P, const
       return GMG_ERR_INVALID_ARG;
     }
     std::vector<char> used(p.n_coarse, 0);
-    for (int64_t i = 0; i < nf; ++i)
+    for (int64_t i = 0; i < nf; ++i) {
+      const double wsum = p.w[3 * i] + p.w[3 * i + 1] + p.w[3 * i + 2];
+      if (std::isfinite(wsum)) *unity_dev = std::max(*unity_dev, std::fabs(wsum - 1.0));
       for (int s = 0; s < 3; ++s) {
         const int32_t k = p.idx[3 * i + s];
         const double w = p.w[3 * i + s];
@@ -1782,6 +1785,7 @@ static gmg_status validate(const gmg_csr* A, int nP, const gmg_prolong* P, const
           used[k] = 1;
         }
       }
+    }
     for (int64_t k = 0; k < p.n_coarse; ++k)
       if (!used[k]) {
         set_error("P[" + std::to_string(l) + "]: coarse point " + std::to_string(k) + " has no fine row");
@@ -1985,7 +1989,8 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
     t_ms[k] += std::chrono::duration<double, std::milli>(t - t_last).count();
     t_last = t;
   };
-  GMG_TRY(validate(A, nP, P, coloring));
+  c->p_unity_dev = 0.0;
+  GMG_TRY(validate(A, nP, P, coloring, &c->p_unity_dev));
   GMG_CK(cudaGetDevice(&c->device));
   GMG_CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
   Arena& a = c->arena;

@@ -186,6 +186,25 @@ def test_single_level_is_direct_solve(gmg):
     g.close()
 
 
+def test_partition_of_unity_warning(gmg):
+    """Barycentric prolongation weights sum to 1 (Sec. 4.4); weights that do
+    not are flagged, not refused, and the solve runs as usual."""
+    s = gi.icosphere_system(4)
+    g = gmg.Solver(s.A, s.Ps)
+    dev = max(float(np.abs(np.asarray(p.w).reshape(-1, 3).sum(1) - 1.0).max()) for p in s.Ps)
+    assert g.warnings == 0 and g.p_unity_dev == pytest.approx(dev, abs=1e-15) and dev <= 1e-12
+    x0, it0, _, _, _ = g.solve(_t(s.b), tol=1e-10)
+    g.close()
+    Ps = [gi.Prolongation(p.n_fine, p.n_coarse, p.idx, np.asarray(p.w) * 1.01) for p in s.Ps]
+    g = gmg.Solver(s.A, Ps)
+    assert g.warnings == gmg.GMG_WARN_P_UNITY and abs(g.p_unity_dev - 0.01) <= 1e-12
+    x, it, rr, _, st = g.solve(_t(s.b), tol=1e-10)
+    # a constant factor on P leaves the coarse correction P (P^T A P)^-1 P^T unchanged up to rounding
+    assert st == 0 and abs(it - it0) <= 1 and rr <= 1e-10
+    close(_np(x), _np(x0), 1e-8, "solution with scaled prolongation weights")
+    g.close()
+
+
 def test_set_values_refresh(gmg):
     s = gi.icosphere_system(4)
     g = gmg.Solver(s.A, s.Ps)
