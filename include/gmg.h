@@ -437,6 +437,17 @@ gmg_status gmg_pivot_reciprocal(int64_t n, const double *d, double *out, void *s
  * pointer with n > 0). */
 gmg_status gmg_convert(int64_t n, int dir, const void *in, void *out, void *stream);
 
+/* Self-test of the bounded device-side wait (no counterpart in the paper).
+ * The cluster-level kernels wait for their streamed matrix entries on an
+ * mbarrier with a limit of polls, after which they set an error word that
+ * gmg_solve reports as GMG_ERR_TIMEOUT, instead of hanging.  This runs that
+ * wait, in one warp, on an mbarrier that nothing arrives on: *timed_out
+ * receives 1 when the wait gave up (the expected outcome), *ms (may be NULL)
+ * its device time.  polls <= 0 uses the limit of the solve kernels.  The
+ * kernel returns normally, so the context stays usable.  Errors: INVALID_ARG
+ * (null timed_out), OOM, CUDA. */
+gmg_status gmg_wait_selftest(int polls, int *timed_out, double *ms, void *stream);
+
 /* ---- allocation-free residual (no counterpart in the paper) ----
  * For callers that cannot allocate device memory (code running inside
  * another framework's memory pool, under an allocator that forbids

@@ -30,7 +30,7 @@ EXPORTED = [
     "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_coarse_solve", "gmg_vcycle", "gmg_profile",
     "gmg_profile_read", "gmg_kernel_launches", "gmg_residual_norm_noalloc", "gmg_setup_ML", "gmg_set_t",
     "gmg_mass", "gmg_grad", "gmg_setup_many", "gmg_solve_many", "gmg_destroy_many", "gmg_autotune", "gmg_set_lanes",
-    "gmg_vcycle_batched", "gmg_pivot_reciprocal", "gmg_convert", "gmg_colour", "gmg_level_path", "gmg_profile_levels", "gmg_grad_pattern",
+    "gmg_vcycle_batched", "gmg_pivot_reciprocal", "gmg_convert", "gmg_colour", "gmg_wait_selftest", "gmg_level_path", "gmg_profile_levels", "gmg_grad_pattern",
     "gmg_autotune_batched", "gmg_set_lanes_batched", "gmg_autotune_many",
     "gmg_build_hierarchy", "gmg_hierarchy_info", "gmg_hierarchy_level", "gmg_destroy_hierarchy",
 ]
@@ -103,6 +103,7 @@ def load_library(path: str | None = None):
         "gmg_pivot_reciprocal": (I, [I64, V, V, V]),
         "gmg_convert": (I, [I64, I, V, V, V]),
         "gmg_colour": (I, [I64, V, V, V, V]),
+        "gmg_wait_selftest": (I, [I, V, V, V]),
         "gmg_level_path": (I, [V, I, V]),
         "gmg_profile": (I, [V, I]),
         "gmg_kernel_launches": (ctypes.c_uint64, []),

@@ -71,9 +71,13 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
                : "memory");
 }
 // Waits for the phase of m with the given parity to complete; gives up after
-// a bounded number of polls (sets *err) so that a lost copy cannot hang the GPU.
-__device__ __forceinline__ void mbar_wait(uint64_t* m, unsigned parity, int* err) {
-  for (int it = 0; it < (1 << 22); ++it) {
+// `polls` polls (sets *err) so that a lost copy cannot hang the GPU.  A
+// failing poll suspends the warp for about 3.8 us on GB300 (measured with
+// gmg_wait_selftest), so the limit gives up after about one second; a poll
+// does not advance while the context is switched out.
+constexpr int kWaitPolls = 1 << 18;
+__device__ __forceinline__ void mbar_wait(uint64_t* m, unsigned parity, int* err, int polls = kWaitPolls) {
+  for (int it = 0; it < polls; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -707,6 +711,20 @@ gmg_status refresh_cluster_values(gmg_ctx* c, cudaStream_t s) {
   return GMG_OK;
 }
 
+// Self-test of the bounded wait: one warp waits on an mbarrier that nothing
+// arrives on, so every poll fails and the wait gives up; elapsed device time
+// in *ns.
+__global__ void k_wait_selftest(int polls, int* err, unsigned long long* ns) {
+  __shared__ uint64_t m;
+  if (threadIdx.x == 0) mbar_init(&m, 1);
+  __syncthreads();
+  unsigned long long t0, t1;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  mbar_wait(&m, 0u, err, polls);
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+  if (threadIdx.x == 0) *ns = t1 - t0;
+}
+
 // GMG_ERR_TIMEOUT once if a cluster-level launch gave up waiting for an
 // entry block (its results are then not to be trusted); clears the flag.
 gmg_status cluster_level_status(gmg_ctx* c, cudaStream_t s) {
@@ -748,3 +766,42 @@ gmg_status launch_cluster_level(gmg_ctx* c, int mode, cudaStream_t s) {
 }
 
 }  // namespace gmg
+
+// The cluster level's bounded wait run on a barrier that never completes
+// (polls <= 0: the limit the solve kernels use).
+extern "C" gmg_status gmg_wait_selftest(int polls, int* timed_out, double* ms, void* stream) {
+  using namespace gmg;
+  if (!timed_out) {
+    set_error("gmg_wait_selftest: null pointer");
+    return GMG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int* err = nullptr;
+  unsigned long long* ns = nullptr;
+  GMG_CK(cudaMalloc((void**)&err, sizeof(int)));
+  if (cudaMalloc((void**)&ns, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaFree(err);
+    set_error("gmg_wait_selftest: cudaMalloc failed");
+    return GMG_ERR_OOM;
+  }
+  int h = 0;
+  unsigned long long hns = 0;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 32, 0, s>>>(polls > 0 ? polls : kWaitPolls, err, ns);
+    ++g_launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hns, ns, sizeof(hns), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(err);
+  cudaFree(ns);
+  if (e != cudaSuccess) {
+    set_error(std::string("gmg_wait_selftest: ") + cudaGetErrorString(e));
+    return GMG_ERR_CUDA;
+  }
+  *timed_out = h;
+  if (ms) *ms = 1e-6 * (double)hns;
+  return GMG_OK;
+}

@@ -205,6 +205,26 @@ def test_partition_of_unity_warning(gmg):
     g.close()
 
 
+def test_bounded_wait_gives_up_and_reports(gmg):
+    """The cluster level's wait for streamed entries is bounded: on a barrier
+    that nothing arrives on it gives up within seconds, reports it, and the
+    context stays usable (a solve that uses the cluster level follows)."""
+    import ctypes
+
+    lib = gmg.load_library()
+    t, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+    assert lib.gmg_wait_selftest(4096, ctypes.byref(t), ctypes.byref(ms), None) == 0
+    assert t.value == 1 and 0.0 < ms.value < 1000.0
+    assert lib.gmg_wait_selftest(0, ctypes.byref(t), ctypes.byref(ms), None) == 0  # the solve kernels' limit
+    assert t.value == 1 and 50.0 < ms.value < 5000.0
+    s = gi.torus_system(512, 256, 1e-4, 3)
+    g = gmg.Solver(s.A, s.Ps, precision=gmg.GMG_FP32_PCG)
+    assert 1 in g.paths  # a level runs as a cluster level, on the bounded waits
+    x, it, rr, _, st = g.solve(_t(s.b), tol=1e-10)
+    assert st == 0 and rr <= 1e-10
+    g.close()
+
+
 def test_set_values_refresh(gmg):
     s = gi.icosphere_system(4)
     g = gmg.Solver(s.A, s.Ps)
