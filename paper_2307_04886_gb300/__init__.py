@@ -159,6 +159,21 @@ def colour(A):
     return out, int(nc.value)
 
 
+def load_hierarchy(path: str):
+    """(prolongations, per-level colourings) saved by Solver.save_hierarchy:
+    pass them as Solver(A, Ps, coloring=colourings)."""
+    from types import SimpleNamespace
+
+    z = np.load(path)
+    nlev = int(z["nlev"][0])
+    Ps = []
+    for l in range(nlev - 1):
+        idx, w = z[f"p{l}_idx"], z[f"p{l}_w"]
+        Ps.append(SimpleNamespace(n_fine=idx.reshape(-1, 3).shape[0], n_coarse=int(z[f"p{l}_n_coarse"][0]),
+                                  idx=idx, w=w))
+    return Ps, [z[f"colour{l}"] for l in range(nlev)]
+
+
 def _stream():
     import torch
 
@@ -229,6 +244,7 @@ class Solver:
                                  _stream()), "gmg_setup")
         self._h = h
         self._lib = lib
+        self._Ps = [(int(P.n_coarse), np.asarray(P.idx, dtype=np.int32), np.asarray(P.w, dtype=np.float64)) for P in Ps]
         nl = ctypes.c_int()
         lib.gmg_num_levels(h, ctypes.byref(nl))
         self.nlev = nl.value
@@ -382,6 +398,19 @@ class Solver:
         _check(self._lib.gmg_level_export(self._h, l, _np_ptr(rp), _np_ptr(ci), _np_ptr(va), _np_ptr(col)),
                "gmg_level_export")
         return sp.csr_matrix((va, ci, rp), shape=(n, n)), col
+
+    def save_hierarchy(self, path: str):
+        """Writes the prolongations and every level's colouring to an .npz file;
+        `load_hierarchy` returns them so that a later Solver on the same system
+        skips the colouring (its caller-colouring path) and starts from them."""
+        arrs = {"nlev": np.array([self.nlev])}
+        for l, (nc, idx, w) in enumerate(self._Ps):
+            arrs[f"p{l}_n_coarse"] = np.array([nc])
+            arrs[f"p{l}_idx"] = idx
+            arrs[f"p{l}_w"] = w
+        for l in range(self.nlev):
+            arrs[f"colour{l}"] = self.level(l)[1]
+        np.savez(path, **arrs)
 
     # ---- single steps of Alg. 2 (device tensors, caller numbering) ----
     def smooth(self, l, x, b, nsweep, descending=False, fp32=False):

@@ -62,7 +62,7 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags=None) 
     if failed:
         raise RuntimeError("nvcc failed for: " + ", ".join(failed))
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs])
+    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs, "-ldl"])
     os.replace(tmp, LIB)
     for o in objs:
         os.remove(o)

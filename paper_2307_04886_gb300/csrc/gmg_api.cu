@@ -324,6 +324,7 @@ gmg_status gmg_setup(gmg_handle* h, const gmg_csr* A, int n_prolong, const gmg_p
 }
 
 gmg_status gmg_set_values(gmg_handle h, const double* val, int mem, void* stream) {
+  NvtxRange nv("gmg_set_values");
   GMG_TRY(check_handle(h));
   if (!val) {
     set_error("gmg_set_values: null values");
@@ -339,6 +340,7 @@ gmg_status gmg_set_values(gmg_handle h, const double* val, int mem, void* stream
 
 gmg_status gmg_solve(gmg_handle h, const double* b, double* x, double tol, int mem, gmg_solve_info* info,
                      void* stream) {
+  NvtxRange nv("gmg_solve");
   GMG_TRY(check_handle(h));
   if (!b || !x || !(tol >= 0.0) || (mem != GMG_MEM_HOST && mem != GMG_MEM_DEVICE)) {
     set_error("gmg_solve: null vector, negative tolerance or bad memory kind");

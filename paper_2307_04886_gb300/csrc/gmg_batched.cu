@@ -540,6 +540,7 @@ using namespace gmg;
 
 extern "C" gmg_status gmg_solve_batched(gmg_handle h, int nrhs, const double* B, double* X, double tol, int mem,
                                         gmg_solve_info* info, void* stream) {
+  gmg::NvtxRange nv("gmg_solve_batched");
   if (!h || !B || !X || nrhs < 1 || nrhs > kMaxRhs || !(tol >= 0.0) ||
       (mem != GMG_MEM_HOST && mem != GMG_MEM_DEVICE)) {
     set_error("gmg_solve_batched: bad handle, vector, nrhs (1..16), tolerance or memory kind");
@@ -1109,6 +1110,7 @@ extern "C" gmg_status gmg_setup_many(gmg_many* out, int nmesh, const gmg_csr* A,
 
 extern "C" gmg_status gmg_solve_many(gmg_many m, int nrhs, const double* const* B, double* const* X, double tol,
                                      int mem, gmg_solve_info* info, void* stream) {
+  gmg::NvtxRange nv("gmg_solve_many");
   if (!m || !B || !X || nrhs < 1 || nrhs > kMaxRhs || !(tol >= 0.0) ||
       (mem != GMG_MEM_HOST && mem != GMG_MEM_DEVICE)) {
     set_error("gmg_solve_many: bad handle, vector list, nrhs (1..16), tolerance or memory kind");

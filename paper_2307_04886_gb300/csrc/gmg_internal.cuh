@@ -10,6 +10,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gmg.h"
 #include "gmg_fpbits.cuh"
 
@@ -95,6 +97,19 @@ inline gmg_status launch(void (*k)(P...), int64_t grid, int block, cudaStream_t 
 }
 
 // Device allocation registry of a handle: everything is freed by gmg_destroy.
+// A named range on the host timeline of a profiler (NVTX; next to no cost
+// when no tool is attached).  next() ends the current range and opens another.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  void next(const char* name) {
+    nvtxRangePop();
+    nvtxRangePushA(name);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct Arena {
   std::vector<void*> ptrs;
   double ms_alloc = 0.0, ms_copy = 0.0;  // host time in cudaMalloc and in uploads (GMG_VERBOSE=1 reports it)

@@ -1984,10 +1984,12 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   const clk::time_point t_start = clk::now();
   double t_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   clk::time_point t_last = t_start;
-  auto lap = [&](int k) {
+  NvtxRange nv("gmg_setup: validation and uploads");
+  auto lap = [&](int k, const char* next = nullptr) {
     const clk::time_point t = clk::now();
     t_ms[k] += std::chrono::duration<double, std::milli>(t - t_last).count();
     t_last = t;
+    if (next) nv.next(next);
   };
   c->p_unity_dev = 0.0;
   GMG_TRY(validate(A, nP, P, coloring, &c->p_unity_dev));
@@ -2043,25 +2045,25 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   auto start_colouring = [&](int l) {
     if (!(coloring && coloring[l])) jobs[l]->start(c->L[l].n, hrp[l].data(), hcol[l].data());
   };
-  lap(0);
+  lap(0, "gmg_setup: symbolic Galerkin product");
   start_colouring(0);
   for (int l = 0; l + 1 < c->nlev; ++l) {
     GMG_TRY(galerkin_symbolic(c, l, s, hrp[l + 1], hcol[l + 1]));
     start_colouring(l + 1);
   }
   locality_ranks(c, hrp, hcol, P);
-  lap(1);
+  lap(1, "gmg_setup: colouring wait");
   for (auto& j : jobs) j->join();
-  lap(2);
+  lap(2, "gmg_setup: level layouts");
   // colouring, renumbering, layouts
   std::vector<std::vector<int32_t>> perm(c->nlev), iperm(c->nlev);
   for (int l = 0; l < c->nlev; ++l)
     GMG_TRY(build_level_structure(c, l, hrp[l].data(), hcol[l].data(), coloring ? coloring[l] : nullptr, *jobs[l],
                                   perm[l], iperm[l]));
-  lap(6);
+  lap(6, "gmg_setup: transfer layouts");
   for (int l = 0; l + 1 < c->nlev; ++l)
     GMG_TRY(build_transfer_structure(c, l, P[l], perm[l], iperm[l], perm[l + 1], iperm[l + 1]));
-  lap(7);
+  lap(7, "gmg_setup: vectors");
   // coarsest dense buffers
   c->nco = c->L[c->nlev - 1].n;
   {
@@ -2093,13 +2095,13 @@ gmg_status setup_impl(gmg_ctx* c, const gmg_csr* A, int nP, const gmg_prolong* P
   GMG_CK(cudaMemset(c->red_cnt, 0, 4 * sizeof(int)));
   GMG_TRY(a.alloc(&c->dhist, (size_t)c->opt.max_iter + 2));
   GMG_CK(cudaMallocHost((void**)&c->h_scal, 64 * sizeof(double)));
-  lap(3);
+  lap(3, "gmg_setup: tail and cluster level");
   GMG_TRY(build_tail(c, hrp, hcol, perm, iperm, P));
   if (c->tail_l0 >= 2) {
     const int l = c->tail_l0 - 1;
     GMG_TRY(build_cluster_level(c, l, hrp[l].data(), hcol[l].data(), perm[l], iperm[l]));
   }
-  lap(4);
+  lap(4, "gmg_setup: numeric set-up");
   const gmg_status st = numeric_setup(c, s, false);
   if (const char* e = std::getenv("GMG_VERBOSE"))
     if (e[0] == '1' && st == GMG_OK) {

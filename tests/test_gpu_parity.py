@@ -225,6 +225,26 @@ def test_bounded_wait_gives_up_and_reports(gmg):
     g.close()
 
 
+def test_saved_hierarchy_gives_the_same_solver(gmg, tmp_path):
+    """A hierarchy checkpoint (prolongations and colourings) reloaded as a
+    caller colouring gives the same levels, colourings and solution bits."""
+    s = gi.torus_system(250, 122, 1e-4, 5)
+    g = gmg.Solver(s.A, s.Ps, precision=gmg.GMG_FP32_PCG)
+    x1 = _np(g.solve(_t(s.b), tol=1e-10)[0])
+    g.save_hierarchy(str(tmp_path / "h.npz"))
+    Ps, cols = gmg.load_hierarchy(str(tmp_path / "h.npz"))
+    g2 = gmg.Solver(s.A, Ps, precision=gmg.GMG_FP32_PCG, coloring=cols)
+    assert g2.nlev == g.nlev and g2.dims == g.dims
+    for l in range(g.nlev):
+        A1, c1 = g.level(l)
+        A2, c2 = g2.level(l)
+        assert np.array_equal(c1, c2) and np.array_equal(A1.data, A2.data)
+    x2 = _np(g2.solve(_t(s.b), tol=1e-10)[0])
+    assert np.array_equal(x1, x2)
+    g.close()
+    g2.close()
+
+
 def test_set_values_refresh(gmg):
     s = gi.icosphere_system(4)
     g = gmg.Solver(s.A, s.Ps)
