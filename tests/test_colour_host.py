@@ -26,6 +26,7 @@ def _cases():
         "torus512x256": lambda: gi.torus_system(512, 256, 1e-4, 3),
         "book_small": lambda: gi.nonmanifold_system(pages=3, n_radial=40, n_spine=60),
         "bilaplacian": lambda: gi.workloads.bilaplacian_system(),
+        "cloud16k": lambda: gi.cloud_system(16384, stop=300),  # kNN pattern, random order, about 20 colours
     }
 
 
