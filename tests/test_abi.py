@@ -66,3 +66,25 @@ def test_null_arguments_are_rejected_without_touching_the_device(lib):
     hh = ctypes.c_void_p()
     assert h.gmg_setup(ctypes.byref(hh), None, 0, None, None, None, None) == lib.GMG_ERR_INVALID_ARG
     assert b"A" in h.gmg_last_error()
+    # the warnings query and the wait self-test refuse null arguments before any device work
+    assert h.gmg_warnings(None, None, None) == lib.GMG_ERR_INVALID_ARG
+    assert h.gmg_wait_selftest(16, None, None, None) == lib.GMG_ERR_INVALID_ARG
+
+
+def test_hierarchy_checkpoint_format(lib, tmp_path):
+    """load_hierarchy reads the .npz layout Solver.save_hierarchy writes
+    (prolongations finest first, one colouring per level)."""
+    import numpy as np
+
+    rng = np.random.default_rng(0)
+    idx0 = rng.integers(0, 5, size=(12, 3)).astype(np.int32)
+    w0 = rng.random((12, 3))
+    idx1 = rng.integers(0, 2, size=(5, 3)).astype(np.int32)
+    w1 = rng.random((5, 3))
+    cols = [rng.integers(0, 3, size=n).astype(np.int32) for n in (12, 5, 2)]
+    np.savez(tmp_path / "h.npz", nlev=np.array([3]), p0_n_coarse=np.array([5]), p0_idx=idx0, p0_w=w0,
+             p1_n_coarse=np.array([2]), p1_idx=idx1, p1_w=w1, colour0=cols[0], colour1=cols[1], colour2=cols[2])
+    Ps, cs = lib.load_hierarchy(str(tmp_path / "h.npz"))
+    assert [(p.n_fine, p.n_coarse) for p in Ps] == [(12, 5), (5, 2)]
+    assert np.array_equal(Ps[0].idx, idx0) and np.array_equal(Ps[1].w, w1)
+    assert len(cs) == 3 and all(np.array_equal(a, b) for a, b in zip(cs, cols))
