@@ -263,6 +263,8 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    import numpy as np
+
     import gmg_inputs as gi
     import oracle
 
@@ -277,6 +279,15 @@ def run_reference(args):
             setups.append(su)
             solves.append(so)
     ms = sum(times) / len(times)
+    # one V-cycle of the oracle alone (FP64, from x = 0), as the paper times its cycles
+    o = oracle.Oracle(s.A, s.Ps, lib_path=path)
+    x0 = np.zeros(s.n)
+    o.vcycle(x0, s.b)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        o.vcycle(x0, s.b)
+    vcycle_ms = (time.perf_counter() - t0) * 1e3 / 3
+    del o
     line = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -284,7 +295,7 @@ def run_reference(args):
         "config": {"workload": WORKLOAD_DESC,
                    "solver": "CPU FP64 oracle: Galerkin setup + colouring + Cholesky + V-cycle-preconditioned CG",
                    "iterations": iters, "setup_ms": sum(setups) / len(setups),
-                   "solve_ms": sum(solves) / len(solves)},
+                   "solve_ms": sum(solves) / len(solves), "vcycle_ms": vcycle_ms},
         "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} full oracle runs (setup + {iters} PCG iterations to 1e-10) on "
                                    f"{cores} host threads (OpenMP over independent rows)"},
