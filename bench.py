@@ -524,10 +524,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gmg", choices=["gmg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--configs", default="icosphere5,heat512k,book5,spheres64,cloud4m?",
+    ap.add_argument("--configs", default="icosphere5,heat512k,book5,spheres64,cloud4m",
                     help="comma-separated other workloads to time after the headline, or 'none'; a trailing '?' "
-                         "times that workload only when its inputs are already cached (cloud4m takes minutes to "
-                         "generate on the host)")
+                         "times that workload only when its inputs are already cached (cloud4m's take one to two "
+                         "minutes to generate on the host, once)")
     ap.add_argument("--profile-step", action="store_true",
                     help="set up, autotune, run `warmup` untimed steps and one step, print a short note and exit "
                          "(the launch sequence a kernel profiler lists; no timing is reported)")

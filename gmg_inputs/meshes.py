@@ -15,6 +15,19 @@ import numpy as np
 
 _PHI = (1.0 + 5.0 ** 0.5) / 2.0
 
+
+def sorted_unique(key: np.ndarray) -> np.ndarray:
+    """np.unique of a 1-D integer array (sorted distinct values) by one sort and
+    a mask of value changes: the same result, and far faster than np.unique on
+    tens of millions of keys with some numpy versions."""
+    s = np.sort(key, kind="stable")
+    if s.size == 0:
+        return s
+    m = np.empty(s.size, dtype=bool)
+    m[0] = True
+    np.not_equal(s[1:], s[:-1], out=m[1:])
+    return s[m]
+
 # Regular icosahedron: 12 vertices at the cyclic permutations of (0, +-1, +-phi),
 # 20 faces, outward orientation.
 _ICO_V = np.array(
@@ -88,9 +101,11 @@ def torus_grid(n_major: int, n_minor: int, R: float = 1.0, r: float = 0.3):
 
 def mesh_edges(F: np.ndarray) -> np.ndarray:
     """Unique undirected edges (i < j) of a triangle list, sorted."""
-    e = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]], axis=0)
+    e = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]], axis=0).astype(np.int64)
     e = np.sort(e, axis=1)
-    return np.unique(e, axis=0)
+    n = int(e.max()) + 1 if e.size else 1
+    key = sorted_unique(e[:, 0] * n + e[:, 1])  # lexicographic order of (i, j) is the order of i n + j
+    return np.stack([key // n, key % n], axis=1)
 
 
 def mean_edge_length(V: np.ndarray, E: np.ndarray) -> float:

@@ -13,6 +13,8 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
+from .meshes import sorted_unique
+
 
 def _csr_sorted(m: sp.spmatrix) -> sp.csr_matrix:
     m = sp.csr_matrix(m)
@@ -78,7 +80,7 @@ def knn_graph(P: np.ndarray, k: int, workers: int = -1):
     j = nb.reshape(-1).astype(np.int64)
     e = np.stack([np.minimum(i, j), np.maximum(i, j)], axis=1)
     e = e[e[:, 0] != e[:, 1]]
-    key = np.unique(e[:, 0] * n + e[:, 1])
+    key = sorted_unique(e[:, 0] * n + e[:, 1])
     E = np.stack([key // n, key % n], axis=1)
     return E, float(d.mean())
 
