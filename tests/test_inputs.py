@@ -125,3 +125,15 @@ def test_knn_laplacian():
     assert L.nnz == P.shape[0] + 2 * E.shape[0]
     # every point keeps at least its own k nearest neighbours
     assert np.diff(L.indptr).min() >= 11
+
+
+def test_sorted_unique_and_edges_match_numpy():
+    """The generators' distinct-key helper gives np.unique's result (sorted,
+    distinct), and mesh_edges the lexicographically sorted distinct edges."""
+    rng = np.random.default_rng(11)
+    for size, hi in ((0, 5), (1, 5), (1000, 50), (20000, 1 << 40)):
+        key = rng.integers(0, hi, size=size, dtype=np.int64)
+        assert np.array_equal(meshes.sorted_unique(key), np.unique(key))
+    V, F = meshes.icosphere(3)
+    e = np.sort(np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]]), axis=1)
+    assert np.array_equal(meshes.mesh_edges(F), np.unique(e, axis=0))
